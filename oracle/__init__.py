@@ -1,0 +1,280 @@
+"""CPU oracle for UT decoding and Compass (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use
+this package.  It is a ctypes wrapper around `oracle.c`, a plain C
+statement of the method (see that file's header for the passages of the
+paper each function follows), built with gcc -O2 -ffp-contract=off.
+It imports nothing from the GPU package.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPACITY", -6: "WIN16"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("z", ctypes.c_float * 4), ("tan_a", ctypes.c_float * 4),
+                ("pitch", ctypes.c_float), ("x_min", ctypes.c_float), ("z_velo", ctypes.c_float)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n_sectors", ctypes.c_int), ("n_candidates", ctypes.c_int)] + [
+        (n, ctypes.c_float) for n in ("qop_max", "tol_win", "tol_kink", "tol_col", "tol_slope",
+                                      "chi2ndof_max", "sigma_hit", "sigma_x_prior",
+                                      "sigma_tx_prior", "z_kink", "kick_k")]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            _lib.orc_decode.restype = ctypes.c_int
+            _lib.orc_decode.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                        ctypes.c_uint64, P, P, P, P, P, P, P, P, ctypes.c_int]
+            _lib.orc_sort_hits.restype = ctypes.c_int
+            _lib.orc_sort_hits.argtypes = [ctypes.c_size_t] + [P] * 12
+            _lib.orc_compass.restype = ctypes.c_int
+            _lib.orc_compass.argtypes = [P, P, ctypes.c_int, P, P, P, P, P, P, P, P,
+                                         P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+            _lib.orc_fit_tracks.restype = ctypes.c_int
+            _lib.orc_fit_tracks.argtypes = [P, P, P, P, P, P, ctypes.c_uint32, P, P,
+                                            P, P, P, P, P, P, P]
+            _lib.orc_fit64_d.restype = ctypes.c_int
+            _lib.orc_fit64_d.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, P, P]
+            _lib.orc_fit32_d.restype = ctypes.c_int
+            _lib.orc_fit32_d.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, P]
+            _lib.orc_max_threads.restype = ctypes.c_int
+        return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+@dataclasses.dataclass
+class Hits:
+    x: np.ndarray
+    z: np.ndarray
+    sector: np.ndarray
+    layer: np.ndarray
+    id: np.ndarray
+    hit_off: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.hit_off[-1])
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"oracle error {ERR_NAMES.get(code, code)} at {where}")
+        self.code = code
+        self.where = where
+
+
+def geom_struct(geom) -> _Geom:
+    g = _Geom()
+    g.S = int(geom.n_sectors)
+    for l in range(4):
+        g.z[l] = float(geom.z[l])
+        g.tan_a[l] = float(geom.tan_stereo[l])
+    g.pitch = float(geom.sector_pitch)
+    g.x_min = float(geom.x_min)
+    g.z_velo = float(geom.z_velo)
+    return g
+
+
+def params_struct(p) -> _Params:
+    s = _Params()
+    for f in dataclasses.fields(p):
+        setattr(s, f.name, getattr(p, f.name))
+    return s
+
+
+def decode(raw, ev_off, n_events, geom, sorted_=True, capacity=None, n_threads=0,
+           raise_on_error=True):
+    """Decode a batch's raw banks (Sec. IV).  Returns (code, Hits, (event, bank))."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint32)
+    ev_off = np.ascontiguousarray(ev_off, dtype=np.uint64)
+    if capacity is None:
+        capacity = 2 * int(ev_off[n_events])
+    cap = max(int(capacity), 1)
+    B = 4 * geom.n_sectors
+    x = np.zeros(cap, np.float32)
+    z = np.zeros(cap, np.float32)
+    sector = np.zeros(cap, np.uint16)
+    layer = np.zeros(cap, np.uint8)
+    hid = np.zeros(cap, np.uint32)
+    hit_off = np.zeros(n_events * B + 1, np.uint32)
+    ee = np.zeros(1, np.int64)
+    eb = np.zeros(1, np.int64)
+    zl = np.ascontiguousarray(geom.z, dtype=np.float32)
+    rc = lib().orc_decode(_p(raw), _p(ev_off), n_events, geom.n_sectors, _p(zl),
+                          geom.sector_pitch, geom.strip_pitch, geom.strips, geom.x_min,
+                          1 if sorted_ else 0, int(capacity), _p(x), _p(z), _p(sector),
+                          _p(layer), _p(hid), _p(hit_off), _p(ee), _p(eb), n_threads)
+    if rc != 0 and raise_on_error:
+        raise OracleError(rc, (int(ee[0]), int(eb[0])))
+    n = int(hit_off[-1]) if rc == 0 else 0
+    hits = Hits(x[:n], z[:n], sector[:n], layer[:n], hid[:n], hit_off)
+    return rc, hits, (int(ee[0]), int(eb[0]))
+
+
+def sort_hits(h: Hits):
+    """Stable per-bank sort of decoded hits by half-strip (Table I permutation)."""
+    n = h.n
+    out = Hits(np.zeros(n, np.float32), np.zeros(n, np.float32), np.zeros(n, np.uint16),
+               np.zeros(n, np.uint8), np.zeros(n, np.uint32), h.hit_off.copy())
+    perm = np.zeros(n, np.uint32)
+    lib().orc_sort_hits(h.hit_off.size - 1, _p(h.hit_off), _p(h.x), _p(h.z), _p(h.sector),
+                        _p(h.layer), _p(h.id), _p(out.x), _p(out.z), _p(out.sector),
+                        _p(out.layer), _p(out.id), _p(perm))
+    return out, perm
+
+
+@dataclasses.dataclass
+class Tracks:
+    hit: np.ndarray       # i32 [T, 4]
+    qop: np.ndarray
+    chi2: np.ndarray
+    x: np.ndarray
+    tx: np.ndarray
+    nhits: np.ndarray
+    found: np.ndarray
+    win: np.ndarray | None
+    near: np.ndarray      # min decision margin per track
+    qop64: np.ndarray
+    chi2_64: np.ndarray
+
+
+def compass(hx, hit_off, n_events, geom, velo, params, want_windows=False, n_threads=0,
+            raise_on_error=True):
+    """Windows + tracklet search + selection (Sec. V) for every VELO track.
+
+    velo: object with x, y, tx, ty (f32), flags (u8), trk_off (u32[E+1]).
+    """
+    hx = np.ascontiguousarray(hx, dtype=np.float32)
+    hit_off = np.ascontiguousarray(hit_off, dtype=np.uint32)
+    T = int(velo.trk_off[n_events])
+    vx = np.ascontiguousarray(velo.x[:T], np.float32)
+    vy = np.ascontiguousarray(velo.y[:T], np.float32)
+    vtx = np.ascontiguousarray(velo.tx[:T], np.float32)
+    vty = np.ascontiguousarray(velo.ty[:T], np.float32)
+    vfl = np.ascontiguousarray(velo.flags[:T], np.uint8)
+    toff = np.ascontiguousarray(velo.trk_off[: n_events + 1], np.uint32)
+    Tn = max(T, 1)
+    out = Tracks(np.full((Tn, 4), -1, np.int32), np.zeros(Tn, np.float32), np.zeros(Tn, np.float32),
+                 np.zeros(Tn, np.float32), np.zeros(Tn, np.float32), np.zeros(Tn, np.uint8),
+                 np.zeros(Tn, np.uint8),
+                 np.full((Tn, 4, params.n_sectors, 2), -1, np.int16) if want_windows else None,
+                 np.zeros(Tn, np.float64), np.zeros(Tn, np.float64), np.zeros(Tn, np.float64))
+    g = geom_struct(geom)
+    pp = params_struct(params)
+    et = np.zeros(1, np.int64)
+    rc = lib().orc_compass(_p(hx), _p(hit_off), n_events, ctypes.byref(g), _p(vx), _p(vy), _p(vtx),
+                           _p(vty), _p(vfl), _p(toff), ctypes.byref(pp), _p(out.hit), _p(out.qop),
+                           _p(out.chi2), _p(out.x), _p(out.tx), _p(out.nhits), _p(out.found),
+                           _p(out.win) if want_windows else None, _p(out.near), _p(out.qop64),
+                           _p(out.chi2_64), _p(et), n_threads)
+    if rc != 0 and raise_on_error:
+        raise OracleError(rc, int(et[0]))
+    if T == 0:
+        out = Tracks(*(a[:0] if isinstance(a, np.ndarray) else a for a in dataclasses.astuple(out)))
+    return out
+
+
+def fit_tracks(hx, geom, velo, hit, params):
+    """Refit given hit sets (float and double).  Returns dict of arrays."""
+    hx = np.ascontiguousarray(hx, dtype=np.float32)
+    hit = np.ascontiguousarray(hit, dtype=np.int32)
+    T = hit.shape[0]
+    vx = np.ascontiguousarray(velo.x[:T], np.float32)
+    vy = np.ascontiguousarray(velo.y[:T], np.float32)
+    vtx = np.ascontiguousarray(velo.tx[:T], np.float32)
+    vty = np.ascontiguousarray(velo.ty[:T], np.float32)
+    o = {k: np.zeros(max(T, 1), np.float32) for k in ("qop", "chi2", "x", "tx")}
+    o["ok"] = np.zeros(max(T, 1), np.uint8)
+    o["qop64"] = np.zeros(max(T, 1), np.float64)
+    o["chi2_64"] = np.zeros(max(T, 1), np.float64)
+    g = geom_struct(geom)
+    pp = params_struct(params)
+    lib().orc_fit_tracks(_p(hx), ctypes.byref(g), _p(vx), _p(vy), _p(vtx), _p(vty), T, _p(hit),
+                         ctypes.byref(pp), _p(o["qop"]), _p(o["chi2"]), _p(o["x"]), _p(o["tx"]),
+                         _p(o["ok"]), _p(o["qop64"]), _p(o["chi2_64"]))
+    return {k: v[:T] for k, v in o.items()}
+
+
+def fit64_d(d, present, t, f, w, px, ptx):
+    """Double-precision p-kick least squares on explicit residuals (Sec. III-C)."""
+    d = np.ascontiguousarray(d, np.float64)
+    pr = np.ascontiguousarray(present, np.int32)
+    t = np.ascontiguousarray(t, np.float64)
+    f = np.ascontiguousarray(f, np.float64)
+    delta = np.zeros(3, np.float64)
+    c2 = np.zeros(1, np.float64)
+    ok = lib().orc_fit64_d(_p(d), _p(pr), _p(t), _p(f), w, px, ptx, _p(delta), _p(c2))
+    return bool(ok), delta, float(c2[0])
+
+
+def fit32_d(d, present, t, f, w, px, ptx):
+    """The float fit on explicit residuals: returns ok, (a, b, q, chi2)."""
+    d = np.ascontiguousarray(d, np.float32)
+    pr = np.ascontiguousarray(present, np.int32)
+    t = np.ascontiguousarray(t, np.float32)
+    f = np.ascontiguousarray(f, np.float32)
+    out = np.zeros(4, np.float32)
+    ok = lib().orc_fit32_d(_p(d), _p(pr), _p(t), _p(f), np.float32(w), np.float32(px),
+                           np.float32(ptx), _p(out))
+    return bool(ok), out
+
+
+class Velo:
+    """VELO tracks view of a synthetic batch."""
+
+    def __init__(self, batch):
+        self.x, self.y, self.tx, self.ty = batch.velo_x, batch.velo_y, batch.velo_tx, batch.velo_ty
+        self.flags = batch.velo_flags
+        self.trk_off = batch.trk_off
+
+
+def run_batch(batch, params, n_threads=0, want_windows=False):
+    """Decode (sorted) + Compass for a whole batch: (Hits, Tracks)."""
+    _, hits, _ = decode(batch.raw, batch.ev_off, batch.n_events, batch.geom, True, n_threads=n_threads)
+    tr = compass(hits.x, hits.hit_off, batch.n_events, batch.geom, Velo(batch), params,
+                 want_windows=want_windows, n_threads=n_threads)
+    return hits, tr

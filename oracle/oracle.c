@@ -1,0 +1,694 @@
+/*
+ * Plain CPU oracle for UT raw-bank decoding and Compass track following.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU path computes.  Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may build or call it; the product
+ * path never does.  It shares no code, header or constant table with the
+ * CUDA library: every definition below is written out here from the paper
+ * and the readings listed with it.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math,
+ * no FMA contraction: every float operation is one IEEE-rounded op, so the
+ * float decisions below are reproducible bit for bit).
+ *
+ * Paper passages followed (A parallel-computing algorithm for high-energy
+ * physics particle tracking and decoding using GPU architectures):
+ *   Sec. IV        raw banks -> hit parameters, SoA + offsets, sector groups
+ *   Table I        hit counting, prefix sum, pre-decode, permutation, gather
+ *   Sec. V-A       window search: extrapolation, sector + neighbours,
+ *                  (first, size) int16 windows, (-1,-1) when empty,
+ *                  valid-track filter (acceptance, not backward)
+ *   Sec. V-B       tracklet finding: anchors in panels 1 and 3, tolerance in
+ *                  2 and 4, >= 3 hits, forward then backward, combined range
+ *                  order, candidate count, chi2 selection
+ *   Sec. III-C     p-kick chi2 fit instead of a Kalman filter
+ *   Sec. V-C       CPU form: windows computed per track right before the
+ *                  tracklet search, OpenMP over events
+ *
+ * Parity status: decode, sort and offsets are pinned (round trip, closed
+ * form, brute force).  The Compass search is pinned by a brute-force search
+ * and by isolated-track recovery; the fits by closed forms.  Selections
+ * against generator truth are reported, not pinned (parity unpinned there:
+ * the paper's numbers are on LHCb samples that are not available).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum {
+    ORC_OK = 0,
+    ORC_ERR_ARG = -1,
+    ORC_ERR_DIR = -2,
+    ORC_ERR_HEADER = -3,
+    ORC_ERR_STRIP = -4,
+    ORC_ERR_CAPACITY = -5,
+    ORC_ERR_WIN16 = -6,
+};
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Decoding (Sec. IV, Table I).
+ *
+ * Per event: dir[B] (word offset of bank b's header in the event), banks in
+ * order.  Bank header: bits 0-15 = n, bits 16-31 = source id (must equal b).
+ * Hit words are 16 bit, two per u32, low half first.  Word fields: strip =
+ * bits 0-9, frac = bit 10, flags = bits 11-15.  Half-strip h = 2*strip+frac.
+ *
+ * Checks per bank, in this order, the first failing one is the bank's
+ * error: directory entry inside the event (header and all hit words),
+ * source id == b, every strip < strips.  The reported error is the one of
+ * the lowest (event, bank); a capacity overflow is reported only when no
+ * bank has an error.
+ * ---------------------------------------------------------------------- */
+
+static int check_bank(const uint32_t* ev, uint64_t nw, int B, int b, int strips,
+                      uint32_t* n_out) {
+    uint64_t d = ev[b];
+    if (d < (uint64_t)B || d + 1 > nw) return ORC_ERR_DIR;
+    uint32_t hdr = ev[d];
+    uint32_t n = hdr & 0xFFFFu;
+    uint32_t src = hdr >> 16;
+    if (d + 1 + (n + 1) / 2 > nw) return ORC_ERR_DIR;
+    if (src != (uint32_t)b) return ORC_ERR_HEADER;
+    const uint16_t* w16 = (const uint16_t*)(ev + d + 1); /* little endian: low half first */
+    for (uint32_t k = 0; k < n; ++k) {
+        uint32_t strip = w16[k] & 0x3FFu;
+        if (strip >= (uint32_t)strips) return ORC_ERR_STRIP;
+    }
+    *n_out = n;
+    return ORC_OK;
+}
+
+/* x at y=0 of half-strip h in sector s: x0_s + (h + 1/2) * (pitch/2),
+ * x0_s = s * sector_pitch + x_min.  Float, one multiply then one add each. */
+static float hit_x(int s, int h, float sector_pitch, float strip_pitch, float x_min) {
+    float x0 = (float)s * sector_pitch + x_min;
+    float hp = strip_pitch * 0.5f;
+    float c = ((float)h + 0.5f) * hp;
+    return x0 + c;
+}
+
+/*
+ * raw/ev_off: the batch; E events, S sectors per layer (B = 4S banks).
+ * z[4]: layer z.  sorted != 0: hits of each bank ordered by (h, word index).
+ * Outputs (capacity entries each): x, zh, sector, layer, id; hit_off[E*B+1].
+ * err_event/err_bank: where the reported error is (-1 for capacity).
+ */
+int orc_decode(const uint32_t* raw, const uint64_t* ev_off, int E, int S,
+               const float* z, float sector_pitch, float strip_pitch, int strips, float x_min,
+               int sorted, uint64_t capacity,
+               float* x, float* zh, uint16_t* sector, uint8_t* layer, uint32_t* id,
+               uint32_t* hit_off, int64_t* err_event, int64_t* err_bank, int n_threads) {
+    set_threads(n_threads);
+    const int B = 4 * S;
+    *err_event = -1;
+    *err_bank = -1;
+    uint32_t* n_bank = (uint32_t*)calloc((size_t)E * B + 1, sizeof(uint32_t));
+    int* ev_err = (int*)calloc((size_t)E, sizeof(int));
+    int* ev_err_bank = (int*)calloc((size_t)E, sizeof(int));
+    if (!n_bank || !ev_err || !ev_err_bank) { free(n_bank); free(ev_err); free(ev_err_bank); return ORC_ERR_ARG; }
+
+    /* Pass 1: hit counts per bank ("calculate number of hits"). */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int e = 0; e < E; ++e) {
+        const uint32_t* ev = raw + ev_off[e];
+        uint64_t nw = ev_off[e + 1] - ev_off[e];
+        if (nw < (uint64_t)B) { ev_err[e] = ORC_ERR_DIR; ev_err_bank[e] = 0; continue; }
+        for (int b = 0; b < B; ++b) {
+            uint32_t n = 0;
+            int rc = check_bank(ev, nw, B, b, strips, &n);
+            if (rc != ORC_OK) { ev_err[e] = rc; ev_err_bank[e] = b; break; }
+            n_bank[(size_t)e * B + b] = n;
+        }
+    }
+    for (int e = 0; e < E; ++e) {
+        if (ev_err[e] != ORC_OK) {
+            int rc = ev_err[e];
+            *err_event = e;
+            *err_bank = ev_err_bank[e];
+            free(n_bank); free(ev_err); free(ev_err_bank);
+            return rc;
+        }
+    }
+
+    /* Exclusive prefix sum over the flattened (event, layer, sector) order. */
+    uint64_t acc = 0;
+    for (size_t i = 0; i < (size_t)E * B; ++i) {
+        hit_off[i] = (uint32_t)acc;
+        acc += n_bank[i];
+        if (acc > 0xFFFFFFFFull) break;
+    }
+    if (acc > capacity || acc > 0xFFFFFFFFull) {
+        free(n_bank); free(ev_err); free(ev_err_bank);
+        return ORC_ERR_CAPACITY;
+    }
+    hit_off[(size_t)E * B] = (uint32_t)acc;
+
+    /* Pass 2: decode each bank; sorted order by a stable insertion sort on
+     * the half-strip key (the permutation step), then the gather. */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int e = 0; e < E; ++e) {
+        const uint32_t* ev = raw + ev_off[e];
+        uint32_t* order = NULL;
+        size_t cap_order = 0;
+        for (int b = 0; b < B; ++b) {
+            uint32_t d = ev[b];
+            uint32_t n = ev[d] & 0xFFFFu;
+            const uint16_t* w16 = (const uint16_t*)(ev + d + 1);
+            int l = b / S, s = b % S;
+            if (n > cap_order) {
+                cap_order = n;
+                order = (uint32_t*)realloc(order, cap_order * sizeof(uint32_t));
+            }
+            for (uint32_t k = 0; k < n; ++k) order[k] = k;
+            if (sorted) {
+                for (uint32_t i = 1; i < n; ++i) {
+                    uint32_t cur = order[i];
+                    int hc = 2 * (w16[cur] & 0x3FF) + ((w16[cur] >> 10) & 1);
+                    uint32_t j = i;
+                    while (j > 0) {
+                        uint32_t prev = order[j - 1];
+                        int hp = 2 * (w16[prev] & 0x3FF) + ((w16[prev] >> 10) & 1);
+                        if (hp <= hc) break;  /* stable: equal keys keep word order */
+                        order[j] = prev;
+                        --j;
+                    }
+                    order[j] = cur;
+                }
+            }
+            uint32_t base = hit_off[(size_t)e * B + b];
+            for (uint32_t r = 0; r < n; ++r) {
+                uint16_t w = w16[order[r]];
+                int strip = w & 0x3FF, frac = (w >> 10) & 1;
+                int h = 2 * strip + frac;
+                uint32_t o = base + r;
+                x[o] = hit_x(s, h, sector_pitch, strip_pitch, x_min);
+                zh[o] = z[l];
+                sector[o] = (uint16_t)s;
+                layer[o] = (uint8_t)l;
+                id[o] = ((uint32_t)l << 24) | ((uint32_t)s << 16) | (uint32_t)w;
+            }
+        }
+        free(order);
+    }
+    free(n_bank); free(ev_err); free(ev_err_bank);
+    return ORC_OK;
+}
+
+/* Stable per-bank sort of decoded hits by half-strip (equivalently by x):
+ * perm[i] = input position of output position i. */
+int orc_sort_hits(size_t n_banks, const uint32_t* hit_off,
+                  const float* x, const float* zh, const uint16_t* sector, const uint8_t* layer,
+                  const uint32_t* id, float* xo, float* zo, uint16_t* so, uint8_t* lo,
+                  uint32_t* ido, uint32_t* perm) {
+    for (size_t b = 0; b < n_banks; ++b) {
+        uint32_t a = hit_off[b], e = hit_off[b + 1];
+        for (uint32_t i = a; i < e; ++i) perm[i] = i;
+        for (uint32_t i = a + 1; i < e; ++i) {
+            uint32_t cur = perm[i];
+            int hc = 2 * (id[cur] & 0x3FF) + ((id[cur] >> 10) & 1);
+            uint32_t j = i;
+            while (j > a) {
+                uint32_t prev = perm[j - 1];
+                int hq = 2 * (id[prev] & 0x3FF) + ((id[prev] >> 10) & 1);
+                if (hq <= hc) break;
+                perm[j] = prev;
+                --j;
+            }
+            perm[j] = cur;
+        }
+        for (uint32_t i = a; i < e; ++i) {
+            uint32_t p = perm[i];
+            xo[i] = x[p]; zo[i] = zh[p]; so[i] = sector[p]; lo[i] = layer[p]; ido[i] = id[p];
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Compass (Sec. V).
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    int n_sectors, n_candidates;
+    float qop_max, tol_win, tol_kink, tol_col, tol_slope, chi2ndof_max;
+    float sigma_hit, sigma_x_prior, sigma_tx_prior, z_kink, kick_k;
+} orc_params;
+
+typedef struct {
+    int S;
+    float z[4], tan_a[4], pitch, x_min, z_velo;
+} orc_geom;
+
+/* Relative margin of a decision a <op> b. */
+static double margin(double a, double b) {
+    double m = fabs(a), t = fabs(b);
+    double den = 1.0;
+    if (m > den) den = m;
+    if (t > den) den = t;
+    return fabs(a - b) / den;
+}
+
+/*
+ * Closed-form p-kick fit in float (Sec. III-C, V-B), the precision in which
+ * the tracklet decisions are taken on both sides.
+ *
+ * Model for the residual d_l of the hit in layer l against the VELO straight
+ * line (both at the track's y):  d_l = a + b*t_l + q*f_l,
+ *   t_l = z_l - z_velo, f_l = k*(z_l - z_kink), unknowns (a, b, q) = (dx, dtx, q/p).
+ * chi2 = sum_l w (d_l - a - b t_l - q f_l)^2 + a^2/sx^2 + b^2/stx^2.
+ * Normal equations solved by an LDL^T factorisation; the order of every
+ * float operation is fixed as written.
+ */
+static int fit32(const float* d, const int* present, const float* t, const float* f,
+                 float w, float px, float ptx, float* a_o, float* b_o, float* q_o, float* chi2_o) {
+    float S0 = 0.f, St = 0.f, Sf = 0.f, Stt = 0.f, Stf = 0.f, Sff = 0.f;
+    float Bd = 0.f, Btd = 0.f, Bfd = 0.f;
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        float wt = w * t[l];
+        float wf = w * f[l];
+        S0 = S0 + w;
+        St = St + wt;
+        Sf = Sf + wf;
+        Stt = Stt + wt * t[l];
+        Stf = Stf + wt * f[l];
+        Sff = Sff + wf * f[l];
+        Bd = Bd + w * d[l];
+        Btd = Btd + wt * d[l];
+        Bfd = Bfd + wf * d[l];
+    }
+    float N11 = S0 + px, N12 = St, N13 = Sf, N22 = Stt + ptx, N23 = Stf, N33 = Sff;
+    float D1 = N11;
+    float L21 = N12 / D1;
+    float L31 = N13 / D1;
+    float D2 = N22 - L21 * N12;
+    float E32 = N23 - L31 * N12;
+    float L32 = E32 / D2;
+    float D3 = N33 - L31 * N13 - L32 * E32;
+    if (!(D1 > 0.f) || !(D2 > 0.f) || !(D3 > 0.f)) return 0;
+    float y1 = Bd;
+    float y2 = Btd - L21 * y1;
+    float y3 = Bfd - L31 * y1 - L32 * y2;
+    float z1 = y1 / D1, z2 = y2 / D2, z3 = y3 / D3;
+    float q = z3;
+    float b = z2 - L32 * q;
+    float a = z1 - L21 * b - L31 * q;
+    float chi2 = 0.f;
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        float r = d[l] - a - b * t[l] - q * f[l];
+        chi2 = chi2 + w * r * r;
+    }
+    chi2 = chi2 + px * a * a + ptx * b * b;
+    *a_o = a; *b_o = b; *q_o = q; *chi2_o = chi2;
+    return 1;
+}
+
+/*
+ * The same least-squares problem in double precision, solved from the
+ * normal equations by Gaussian elimination with partial pivoting (the plain
+ * definition).  d, t, f per layer; basis f is the kick shape.  Returns 0 if
+ * singular.
+ */
+int orc_fit64_d(const double* d, const int* present, const double* t, const double* f,
+                double w, double px, double ptx, double* delta, double* chi2_o) {
+    double N[3][4];
+    memset(N, 0, sizeof(N));
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        double g[3] = {1.0, t[l], f[l]};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) N[i][j] += w * g[i] * g[j];
+            N[i][3] += w * g[i] * d[l];
+        }
+    }
+    N[0][0] += px;
+    N[1][1] += ptx;
+    /* Equilibrate (symmetric diagonal scaling) before elimination: the
+     * prior makes the diagonal span ~6 decades. */
+    double sc[3];
+    for (int i = 0; i < 3; ++i) {
+        if (!(N[i][i] > 0.0)) return 0;
+        sc[i] = 1.0 / sqrt(N[i][i]);
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) N[i][j] *= sc[i] * sc[j];
+        N[i][3] *= sc[i];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(N[r][c]) > fabs(N[p][c])) p = r;
+        if (N[p][c] == 0.0) return 0;
+        if (p != c)
+            for (int k = 0; k < 4; ++k) { double tmp = N[c][k]; N[c][k] = N[p][k]; N[p][k] = tmp; }
+        for (int r = c + 1; r < 3; ++r) {
+            double m = N[r][c] / N[c][c];
+            for (int k = c; k < 4; ++k) N[r][k] -= m * N[c][k];
+        }
+    }
+    double x[3];
+    for (int r = 2; r >= 0; --r) {
+        double s = N[r][3];
+        for (int k = r + 1; k < 3; ++k) s -= N[r][k] * x[k];
+        x[r] = s / N[r][r];
+    }
+    for (int i = 0; i < 3; ++i) x[i] *= sc[i];
+    double chi2 = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        double r = d[l] - x[0] - x[1] * t[l] - x[2] * f[l];
+        chi2 += w * r * r;
+    }
+    chi2 += px * x[0] * x[0] + ptx * x[1] * x[1];
+    delta[0] = x[0]; delta[1] = x[1]; delta[2] = x[2];
+    *chi2_o = chi2;
+    return 1;
+}
+
+/* Straight VELO extrapolation to layer l in the measured coordinate
+ * u_l = x_v(z_l) - y_v(z_l) tan(a_l), in double from the float state, and
+ * its split into a float pair (hi, lo) so that a float residual
+ * d = (x - hi) - lo keeps the accuracy of the double prediction. */
+static void extrapolate(const orc_geom* g, float vx, float vy, float vtx, float vty,
+                        double* u, float* uhi, float* ulo) {
+    for (int l = 0; l < 4; ++l) {
+        double dz = (double)g->z[l] - (double)g->z_velo;
+        double xv = (double)vx + (double)vtx * dz;
+        double yv = (double)vy + (double)vty * dz;
+        u[l] = xv - yv * (double)g->tan_a[l];
+        uhi[l] = (float)u[l];
+        ulo[l] = (float)(u[l] - (double)uhi[l]);
+    }
+}
+
+typedef struct {
+    int n;            /* hits in the combined range */
+    int cap;
+    uint32_t* idx;    /* global hit index in combined order */
+} range_t;
+
+static void range_push(range_t* r, uint32_t v) {
+    if (r->n == r->cap) {
+        r->cap = r->cap ? 2 * r->cap : 64;
+        r->idx = (uint32_t*)realloc(r->idx, (size_t)r->cap * sizeof(uint32_t));
+    }
+    r->idx[r->n++] = v;
+}
+
+/*
+ * compass: windows + tracklet search + selection for every VELO track.
+ *
+ * hx: sorted hit x (per bank ascending), hit_off[E*B+1].
+ * Per track outputs: hit[T*4] (global hit index per layer, -1 if none),
+ * qop, chi2, xo, txo, nhits, found; win (nullable) int16 [T][4][n_sec][2];
+ * near (min decision margin of the track, +inf if no decision);
+ * qop64/chi2_64: the double fit of the selected hits (0 if not found).
+ * Returns ORC_ERR_WIN16 (first track in order) if a window does not fit int16.
+ */
+int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom* g,
+                const float* vx, const float* vy, const float* vtx, const float* vty,
+                const uint8_t* vflags, const uint32_t* trk_off, const orc_params* p,
+                int32_t* hit, float* qop, float* chi2, float* xo, float* txo,
+                uint8_t* nhits, uint8_t* found, int16_t* win, double* near_m,
+                double* qop64, double* chi2_64, int64_t* err_track, int n_threads) {
+    set_threads(n_threads);
+    const int S = g->S, B = 4 * S;
+    const int nsec = p->n_sectors;
+    if (nsec < 1 || nsec > 5 || p->n_candidates < 1) return ORC_ERR_ARG;
+    static const int slot_off[5] = {0, -1, 1, -2, 2};
+    const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
+    const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
+    const float ptx = 1.0f / (p->sigma_tx_prior * p->sigma_tx_prior);
+    float t[4], f[4], hw[4];
+    const float kq = p->kick_k * p->qop_max;
+    for (int l = 0; l < 4; ++l) {
+        t[l] = g->z[l] - g->z_velo;
+        f[l] = p->kick_k * (g->z[l] - p->z_kink);
+        hw[l] = kq * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+    }
+    const float slope_tol = kq + p->tol_slope;
+    const double x_max = (double)g->x_min + (double)S * (double)g->pitch;
+    const uint32_t T = trk_off[E];
+    int64_t first_err = -1;
+
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int e = 0; e < E; ++e) {
+        range_t R[4] = {{0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}};
+        float* dv[4] = {NULL, NULL, NULL, NULL};
+        int dcap[4] = {0, 0, 0, 0};
+        for (uint32_t tr = trk_off[e]; tr < trk_off[e + 1]; ++tr) {
+            double mm = INFINITY;
+            for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = -1;
+            qop[tr] = 0.f; chi2[tr] = 0.f; xo[tr] = vx[tr]; txo[tr] = vtx[tr];
+            nhits[tr] = 0; found[tr] = 0; qop64[tr] = 0.0; chi2_64[tr] = 0.0;
+            if (win)
+                for (int k = 0; k < 4 * nsec * 2; ++k) win[(size_t)tr * 4 * nsec * 2 + k] = -1;
+
+            /* Valid-track filter (Sec. V-A): not backward, in acceptance. */
+            if (vflags[tr] & 1u) { near_m[tr] = mm; continue; }
+            double u[4];
+            float uhi[4], ulo[4];
+            extrapolate(g, vx[tr], vy[tr], vtx[tr], vty[tr], u, uhi, ulo);
+            double m0 = margin(u[0], (double)g->x_min), m1 = margin(u[0], x_max);
+            if (m0 < mm) mm = m0;
+            if (m1 < mm) mm = m1;
+            if (u[0] < (double)g->x_min || u[0] > x_max) { near_m[tr] = mm; continue; }
+
+            /* Windows (Sec. V-A): central sector, then neighbours. */
+            int any = 0;
+            for (int l = 0; l < 4; ++l) {
+                R[l].n = 0;
+                double q = (u[l] - (double)g->x_min) / (double)g->pitch;
+                double fq = floor(q);
+                double mq = margin(q, fq) < margin(q, fq + 1.0) ? margin(q, fq) : margin(q, fq + 1.0);
+                if (mq < mm) mm = mq;
+                int c = (int)fq;
+                if (c < 0) c = 0;
+                if (c > S - 1) c = S - 1;
+                uint32_t layer_start = hit_off[(size_t)e * B + (size_t)l * S];
+                for (int k = 0; k < nsec; ++k) {
+                    int s = c + slot_off[k];
+                    if (s < 0 || s >= S) continue;
+                    uint32_t a = hit_off[(size_t)e * B + (size_t)l * S + s];
+                    uint32_t bnd = hit_off[(size_t)e * B + (size_t)l * S + s + 1];
+                    int64_t first = -1, last = -1;
+                    for (uint32_t j = a; j < bnd; ++j) {
+                        float dj = (hx[j] - uhi[l]) - ulo[l];
+                        double ma = margin(dj, -hw[l]), mb = margin(dj, hw[l]);
+                        if (ma < mm) mm = ma;
+                        if (mb < mm) mm = mb;
+                        if (dj >= -hw[l] && dj <= hw[l]) {
+                            if (first < 0) first = j;
+                            last = j;
+                        }
+                    }
+                    if (first < 0) continue;
+                    for (int64_t j = first; j <= last; ++j) range_push(&R[l], (uint32_t)j);
+                    any = 1;
+                    if (win) {
+                        int64_t rel = first - (int64_t)layer_start, sz = last - first + 1;
+                        int16_t* wp = win + (((size_t)tr * 4 + l) * nsec + k) * 2;
+                        if (rel > 32767 || sz > 32767) {
+#pragma omp critical
+                            { if (first_err < 0 || (int64_t)tr < first_err) first_err = tr; }
+                        } else {
+                            wp[0] = (int16_t)rel;
+                            wp[1] = (int16_t)sz;
+                        }
+                    }
+                }
+                if (dcap[l] < R[l].n) {
+                    dcap[l] = R[l].n;
+                    dv[l] = (float*)realloc(dv[l], (size_t)dcap[l] * sizeof(float));
+                }
+                for (int i = 0; i < R[l].n; ++i) dv[l][i] = (hx[R[l].idx[i]] - uhi[l]) - ulo[l];
+            }
+            if (!any) { near_m[tr] = mm; continue; }
+
+            /* Tracklet search (Sec. V-B): forward anchors (0,2) collecting
+             * (1,3); backward anchors (3,1) collecting (2,0) only when the
+             * forward pass found no valid tracklet. */
+            static const int dirs[2][4] = {{0, 2, 1, 3}, {3, 1, 2, 0}};
+            int best_n = 0;
+            float best_chi2 = 0.f, best_q = 0.f, best_a = 0.f, best_b = 0.f;
+            int32_t best_hit[4] = {-1, -1, -1, -1};
+            for (int dir = 0; dir < 2; ++dir) {
+                const int la = dirs[dir][0], lb = dirs[dir][1];
+                const int lc[2] = {dirs[dir][2], dirs[dir][3]};
+                const float dzab = g->z[lb] - g->z[la];
+                const float dzk = p->z_kink - g->z[la];
+                const float dzc[2] = {g->z[lc[0]] - g->z[la], g->z[lc[1]] - g->z[la]};
+                int count = 0;
+                for (int ia = 0; ia < R[la].n && count < p->n_candidates; ++ia) {
+                    const float da = dv[la][ia];
+                    for (int ib = 0; ib < R[lb].n && count < p->n_candidates; ++ib) {
+                        const float db = dv[lb][ib];
+                        const float sr = (db - da) / dzab;
+                        double m;
+                        m = margin(fabsf(sr), slope_tol);
+                        if (m < mm) mm = m;
+                        if (!(fabsf(sr) <= slope_tol)) continue;
+                        const float dk = da + sr * dzk;
+                        m = margin(fabsf(dk), p->tol_kink);
+                        if (m < mm) mm = m;
+                        if (!(fabsf(dk) <= p->tol_kink)) continue;
+                        float dl[4];
+                        int present[4] = {0, 0, 0, 0};
+                        int32_t hsel[4] = {-1, -1, -1, -1};
+                        dl[la] = da; present[la] = 1; hsel[la] = (int32_t)R[la].idx[ia];
+                        dl[lb] = db; present[lb] = 1; hsel[lb] = (int32_t)R[lb].idx[ib];
+                        int nh = 2;
+                        for (int ci = 0; ci < 2; ++ci) {
+                            const int l = lc[ci];
+                            const float pred = da + sr * dzc[ci];
+                            int bi = -1;
+                            float bd = 0.f;
+                            for (int j = 0; j < R[l].n; ++j) {
+                                const float dist = fabsf(dv[l][j] - pred);
+                                m = margin(dist, p->tol_col);
+                                if (m < mm) mm = m;
+                                if (!(dist <= p->tol_col)) continue;
+                                if (bi >= 0) {
+                                    m = margin(dist, bd);
+                                    if (m < mm) mm = m;
+                                }
+                                if (bi < 0 || dist < bd) { bi = j; bd = dist; }
+                            }
+                            if (bi >= 0) {
+                                dl[l] = dv[l][bi]; present[l] = 1; hsel[l] = (int32_t)R[l].idx[bi];
+                                ++nh;
+                            }
+                        }
+                        if (nh < 3) continue;
+                        for (int l = 0; l < 4; ++l) if (!present[l]) dl[l] = 0.f;
+                        float a, b, q, c2;
+                        if (!fit32(dl, present, t, f, w, px, ptx, &a, &b, &q, &c2)) continue;
+                        const float c2n = c2 / (float)(nh - 1);
+                        m = margin(c2n, p->chi2ndof_max);
+                        if (m < mm) mm = m;
+                        if (!(c2n <= p->chi2ndof_max)) continue;
+                        ++count;
+                        if (best_n > 0 && nh == best_n) {
+                            m = margin(c2, best_chi2);
+                            if (m < mm) mm = m;
+                        }
+                        if (nh > best_n || (nh == best_n && c2 < best_chi2)) {
+                            best_n = nh; best_chi2 = c2; best_q = q; best_a = a; best_b = b;
+                            for (int l = 0; l < 4; ++l) best_hit[l] = hsel[l];
+                        }
+                    }
+                }
+                if (count > 0) break;
+            }
+            near_m[tr] = mm;
+            if (best_n == 0) continue;
+            for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = best_hit[l];
+            qop[tr] = best_q;
+            chi2[tr] = best_chi2;
+            xo[tr] = vx[tr] + best_a;
+            txo[tr] = vtx[tr] + best_b;
+            nhits[tr] = (uint8_t)best_n;
+            found[tr] = 1;
+            /* The double fit of the selected hits, for the q/p comparison. */
+            double d64[4] = {0, 0, 0, 0}, t64[4], f64[4], delta[3], c64;
+            int pr[4];
+            for (int l = 0; l < 4; ++l) {
+                pr[l] = best_hit[l] >= 0;
+                t64[l] = (double)g->z[l] - (double)g->z_velo;
+                f64[l] = (double)p->kick_k * ((double)g->z[l] - (double)p->z_kink);
+                if (pr[l]) d64[l] = (double)hx[best_hit[l]] - u[l];
+            }
+            double sh = (double)p->sigma_hit, sx = (double)p->sigma_x_prior, st = (double)p->sigma_tx_prior;
+            if (orc_fit64_d(d64, pr, t64, f64, 1.0 / (sh * sh), 1.0 / (sx * sx), 1.0 / (st * st), delta, &c64)) {
+                qop64[tr] = delta[2];
+                chi2_64[tr] = c64;
+            }
+        }
+        for (int l = 0; l < 4; ++l) { free(R[l].idx); free(dv[l]); }
+    }
+    (void)T;
+    *err_track = first_err;
+    return first_err >= 0 ? ORC_ERR_WIN16 : ORC_OK;
+}
+
+/*
+ * Standalone fit of given hits (the refit step): for each track, hits
+ * hit[T*4] (-1 = absent) are fitted in float (same arithmetic as the
+ * search) and in double.  Outputs per track: q/p, chi2, x, tx (float) and
+ * q/p, chi2 (double).  Tracks with fewer than 3 hits get zeros and ok = 0.
+ */
+int orc_fit_tracks(const float* hx, const orc_geom* g, const float* vx, const float* vy,
+                   const float* vtx, const float* vty, uint32_t T, const int32_t* hit,
+                   const orc_params* p, float* qop, float* chi2, float* xo, float* txo,
+                   uint8_t* ok, double* qop64, double* chi2_64) {
+    const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
+    const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
+    const float ptx = 1.0f / (p->sigma_tx_prior * p->sigma_tx_prior);
+    float t[4], f[4];
+    double t64[4], f64[4];
+    for (int l = 0; l < 4; ++l) {
+        t[l] = g->z[l] - g->z_velo;
+        f[l] = p->kick_k * (g->z[l] - p->z_kink);
+        t64[l] = (double)g->z[l] - (double)g->z_velo;
+        f64[l] = (double)p->kick_k * ((double)g->z[l] - (double)p->z_kink);
+    }
+    double sh = (double)p->sigma_hit, sx = (double)p->sigma_x_prior, st = (double)p->sigma_tx_prior;
+    for (uint32_t tr = 0; tr < T; ++tr) {
+        double u[4];
+        float uhi[4], ulo[4];
+        extrapolate(g, vx[tr], vy[tr], vtx[tr], vty[tr], u, uhi, ulo);
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        double d64[4] = {0, 0, 0, 0};
+        int pr[4], n = 0;
+        for (int l = 0; l < 4; ++l) {
+            int32_t h = hit[(size_t)tr * 4 + l];
+            pr[l] = h >= 0;
+            if (pr[l]) {
+                d[l] = (hx[h] - uhi[l]) - ulo[l];
+                d64[l] = (double)hx[h] - u[l];
+                ++n;
+            }
+        }
+        qop[tr] = 0.f; chi2[tr] = 0.f; xo[tr] = vx[tr]; txo[tr] = vtx[tr]; ok[tr] = 0;
+        qop64[tr] = 0.0; chi2_64[tr] = 0.0;
+        if (n < 3) continue;
+        float a, b, q, c2;
+        if (fit32(d, pr, t, f, w, px, ptx, &a, &b, &q, &c2)) {
+            qop[tr] = q; chi2[tr] = c2; xo[tr] = vx[tr] + a; txo[tr] = vtx[tr] + b; ok[tr] = 1;
+        }
+        double delta[3], c64;
+        if (orc_fit64_d(d64, pr, t64, f64, 1.0 / (sh * sh), 1.0 / (sx * sx), 1.0 / (st * st), delta, &c64)) {
+            qop64[tr] = delta[2];
+            chi2_64[tr] = c64;
+        }
+    }
+    return ORC_OK;
+}
+
+/* The float fit on explicit residuals (exposed for tests of its arithmetic). */
+int orc_fit32_d(const float* d, const int* present, const float* t, const float* f,
+                float w, float px, float ptx, float* out4) {
+    return fit32(d, present, t, f, w, px, ptx, &out4[0], &out4[1], &out4[2], &out4[3]);
+}
