@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark: UT decode + Compass events/s on one GB300.
+
+A step is one pass of the whole path (raw-bank decoding with the per-sector
+sort, window search, tracklet finding, q/p fit) over one batch of seeded
+synthetic events whose shapes follow the paper's workloads (the LHCb
+minbias samples themselves are not available).  Default workload: 1000
+events, 4 planes x 256 sectors, 4000 hits and 200 VELO tracks per event.
+
+Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
+launching stream, the L2 flushed (256 MB write) before every step, bracketed
+by a barrier and a device synchronise; max over ranks.  One JSON line.
+
+--impl reference times the CPU oracle (the plain C statement of the
+method) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UT decode+Compass events/s on 1 GB300, % HBM roofline, p99 batch latency"
+WORKLOADS = {
+    "plain": dict(name="plain", n_events=1000, n_sectors=256, tracks=200, hits=4000, seed=2),
+    "batched": dict(name="batched", n_events=20000, n_sectors=256, tracks=None, hits="lognormal", seed=3),
+    "tiny": dict(name="tiny", n_events=16, n_sectors=64, tracks=100, hits=1500, seed=1),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
+    ap.add_argument("--form", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--tracks-per-warp", type=int, default=1)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_batch(wl, rank):
+    import synth
+    c = dict(WORKLOADS[wl])
+    c.pop("name")
+    c["seed"] = c["seed"] + 1000 * rank
+    return synth.generate(**c)
+
+
+def workload_config(wl, batch, form, extra=None):
+    c = WORKLOADS[wl]
+    cfg = {"workload": f"{wl}: {c['n_events']} events, 4x{c['n_sectors']} sectors, "
+                       f"hits/event {c['hits']}, tracks/event {c['tracks'] or '0.05*hits'}",
+           "n_events": batch.n_events, "hits_per_event": round(batch.n_hits / batch.n_events, 1),
+           "tracks_per_event": round(batch.n_tracks / batch.n_events, 1),
+           "n_sectors_searched": 5, "n_candidates": 8, "form": form,
+           "l2": "flushed before every step (256 MB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(batch, params, min_seconds=10.0):
+    """The oracle as it stands, OpenMP over events on all host threads."""
+    import oracle
+    threads = oracle.max_threads()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.run_batch(batch, params, n_threads=threads)
+        n += batch.n_events
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": n / el, "unit": "events/s", "cores": threads, "kind": "oracle",
+            "sample": f"the full {batch.n_events}-event workload, repeated {n // batch.n_events}x "
+                      f"({el:.1f} s), decode+sort+windows+tracklets+float and double fits"}
+
+
+def run_reference(args):
+    import synth
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    batch = make_batch(args.workload, 0)
+    params = synth.CompassParams()
+    sample_events = min(batch.n_events, 200)
+    sub = synth.subset(batch, 0, sample_events)
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.run_batch(sub, params, n_threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_batch(sub, params, n_threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sample_events * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": workload_config(args.workload, batch, "cpu-oracle",
+                                      {"sample_events_per_step": sample_events}),
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {sample_events} events of the workload per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_bytes(batch):
+    """Minimum bytes each kernel must move for one batch."""
+    E, B, H, T = batch.n_events, batch.geom.n_banks, batch.n_hits, batch.n_tracks
+    raw = 4 * int(batch.ev_off[-1]) + 8 * (E + 1)
+    decode = raw + 4 * (E * B + 1) + 15 * H
+    # find: hit x of the searched banks (<= all hits), offsets, VELO state, outputs
+    find = 4 * H + 4 * (E * B + 1) + 17 * T + 4 * (E + 1) + 34 * T
+    sort_b = 2 * 15 * H + 4 * (E * B + 1)
+    fit = 17 * T + 16 * T + 16 * T + 4 * 4 * T
+    return {"ut_decode": decode, "compass_find": find, "ut_sort_hits": sort_b, "compass_fit": fit}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import synth
+    import paper_2002_11529_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g.build.build()
+
+    batch = make_batch(args.workload, rank)
+    params = synth.CompassParams()
+    ctx = g.Context(batch.geom)
+    pipe = g.Pipeline(ctx, batch, params)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    tpw, blk = args.tracks_per_warp, args.block
+    E = batch.n_events
+
+    kern = ["ut_decode", "ut_sort_hits", "compass_find", "compass_fit"] if args.form == "plain" \
+        else ["ut_decode", "compass_find"]
+
+    def step(ev=None):
+        """One pass; ev: list of (start, end) event pairs per kernel."""
+        def mark(i, which):
+            if ev is not None:
+                ev[i][which].record(stream)
+        if args.form == "plain":
+            mark(0, 0)
+            g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, False, pipe.workspace, stream)
+            mark(0, 1); mark(1, 0)
+            g.ut_sort_hits(ctx, pipe.hits_a, pipe.hits_b, E, stream=stream)
+            pipe.hits_b.hit_off = pipe.hits_a.hit_off
+            mark(1, 1); mark(2, 0)
+            g.compass_find(ctx, pipe.hits_b, pipe.velo, E, params, pipe.tracks, tracks_per_warp=tpw,
+                           block=blk, stream=stream)
+            mark(2, 1); mark(3, 0)
+            g.compass_fit(ctx, pipe.hits_b, pipe.velo, params, pipe.tracks, stream=stream)
+            mark(3, 1)
+        else:
+            mark(0, 0)
+            g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, True, pipe.workspace, stream)
+            mark(0, 1); mark(1, 0)
+            g.compass_find(ctx, pipe.hits_a, pipe.velo, E, params, pipe.tracks, tracks_per_warp=tpw,
+                           block=blk, stream=stream)
+            mark(1, 1)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.check(stream, "warm-up")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region -------------------------------------------------
+    nk = len(kern)
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nk)]
+           for _ in range(args.steps)]
+    step_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    clocks = Clocks(local) if rank == 0 else None
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step_ev[k][0].record(stream)
+        step(evs[k])
+        step_ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if clocks else None
+    ctx.check(stream, "timed region")
+    step_ms = [step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(args.steps)]
+    kern_ms = {kern[i]: [evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)] for i in range(nk)}
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * E * args.steps / (tot_ms / 1e3)
+
+    # ---- end to end through host buffers ------------------------------------
+    h_raw = pipe.raw.cpu().pin_memory()
+    h_ev = pipe.ev_off.cpu().pin_memory()
+    h_velo = [getattr(pipe.velo, n).cpu().pin_memory() for n in ("x", "y", "tx", "ty", "flags", "trk_off")]
+    d_velo = [getattr(pipe.velo, n) for n in ("x", "y", "tx", "ty", "flags", "trk_off")]
+    outs = [pipe.tracks.hit, pipe.tracks.qop, pipe.tracks.chi2, pipe.tracks.x, pipe.tracks.tx,
+            pipe.tracks.nhits, pipe.tracks.found]
+    h_outs = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    h2d = sum(t.numel() * t.element_size() for t in [h_raw, h_ev] + h_velo)
+    d2h = sum(t.numel() * t.element_size() for t in h_outs)
+
+    def e2e_step():
+        pipe.raw.copy_(h_raw, non_blocking=True)
+        pipe.ev_off.copy_(h_ev, non_blocking=True)
+        for d, h in zip(d_velo, h_velo):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, d in zip(h_outs, outs):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    barrier()
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    ctx.check(stream, "e2e")
+    e2e_value = world * E * args.steps / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of each kernel (algorithmic bytes / mean launch time) -----
+    hbm, peak_kind = peaks()
+    algo = algorithmic_bytes(batch)
+    kinfo = {}
+    for name in kern:
+        ms = statistics.mean(kern_ms[name])
+        gbs = algo[name] / (ms / 1e3) / 1e9
+        kinfo[name] = {"ms": round(ms, 5), "algorithmic_bytes": algo[name], "achieved_gbs": round(gbs, 1),
+                       "frac": round(gbs / hbm, 4), "share": round(ms / (tot_ms / args.steps), 3)}
+    dom = max(kern, key=lambda n: kinfo[n]["ms"])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kinfo[dom]["achieved_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": kinfo[dom]["frac"], "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    lat = sorted(step_ms)
+    p = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generator standing in for the LHCb minbias sample)",
+        "config": workload_config(args.workload, batch, args.form,
+                                  {"tracks_per_warp": tpw, "block": blk,
+                                   "parallelism": f"events sharded, {world} independent replicas" if world > 1
+                                   else "single GPU"}),
+        "latency_ms": {"p50": p(0.5), "p99": p(0.99), "what": "one step = one batch"},
+        "roofline": roof,
+        "kernels": kinfo,
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": nk * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(batch, params)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

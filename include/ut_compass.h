@@ -1,0 +1,201 @@
+/*
+ * ut_compass.h -- C ABI of the GB300 UT decoding + Compass library.
+ *
+ * The library decodes Upstream Tracker raw banks into hits and runs Compass
+ * track following (extend each VELO track through the four UT layers, pick
+ * its best hit combination, fit q/p), as described in "A parallel-computing
+ * algorithm for high-energy physics particle tracking and decoding using GPU
+ * architectures" (Sec. IV decoding, Sec. V Compass).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or held in the structs below are DEVICE pointers,
+ *     allocated and owned by the caller; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void*; calls only enqueue work on
+ *     it and return at once (except ut_status and ut_decode_count, which
+ *     synchronise the stream).
+ *   - Return value: UT_OK (0), or a negative UT_ERR_* code for an error the
+ *     host detects before enqueuing (nothing is enqueued then).
+ *   - Errors found on the device (bad raw data, overflow, a bounded wait
+ *     that ran out) are recorded in the context's status word: the error
+ *     with the smallest (event, bank-or-track) wins, deterministically.
+ *     Read it with ut_status.  Kernels never trap.
+ *   - Outputs are unspecified when the status reports an error.
+ *   - Calls that share a context may run on different streams; they then
+ *     share the status word.
+ */
+#ifndef UT_COMPASS_H
+#define UT_COMPASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    UT_OK = 0,
+    UT_ERR_ARG = -1,      /* bad argument (host check)                          */
+    UT_ERR_DIR = -2,      /* bank directory entry points outside its event     */
+    UT_ERR_HEADER = -3,   /* bank header source id differs from the bank index */
+    UT_ERR_STRIP = -4,    /* hit word with strip >= geometry.strips            */
+    UT_ERR_CAPACITY = -5, /* more hits than ut_hits.capacity (or 2^32-1)       */
+    UT_ERR_WIN16 = -6,    /* a window does not fit the int16 (first, size)     */
+    UT_ERR_TIMEOUT = -7,  /* a bounded device-side wait ran out                */
+    UT_ERR_CUDA = -8      /* a CUDA runtime call failed                        */
+};
+
+/* Detector description (Sec. III-A: four planes UTaX, UTaU, UTbV, UTbX, the
+ * U/V planes tilted by +-5 degrees).  Plane l has S = n_sectors sectors of
+ * width sector_pitch along the measured coordinate u ("x at y = 0"), the
+ * first starting at x_min; each sector has `strips` strips of strip_pitch.
+ * A strip of plane l is the line x = u + y * tan_stereo[l]. */
+typedef struct ut_geometry {
+    int n_sectors;          /* S; banks per event B = 4*S, bank b = l*S + s  */
+    float z[4];             /* plane z (mm)                                  */
+    float tan_stereo[4];    /* tan of the strip angle                        */
+    float sector_pitch;     /* 96 mm                                         */
+    float strip_pitch;      /* 0.187 mm                                      */
+    int strips;             /* 512                                           */
+    float x_min;            /* -S*sector_pitch/2                             */
+    float z_velo;           /* z of the VELO state (770 mm)                  */
+} ut_geometry;
+
+/* Decoded hits, structure of arrays (Sec. IV).  Hits of bank (e, l, s) sit
+ * at [hit_off[e*B + l*S + s], hit_off[e*B + l*S + s + 1]).  hit_off has
+ * E*B + 1 entries (exclusive prefix sum over banks; last = total).
+ * Each array holds `capacity` entries. */
+typedef struct ut_hits {
+    float* x;               /* x at y = 0 (mm)                               */
+    float* z;               /* plane z (mm)                                  */
+    uint16_t* sector;       /* s                                             */
+    uint8_t* layer;         /* l                                             */
+    uint32_t* id;           /* (l << 24) | (s << 16) | 16-bit hit word       */
+    uint32_t* hit_off;      /* E*B + 1 offsets                               */
+    uint32_t capacity;
+} ut_hits;
+
+/* VELO tracks, state at z = z_velo, event-major (tracks of event e are
+ * [trk_off[e], trk_off[e+1])). flags bit 0 = backward. */
+typedef struct velo_tracks {
+    const float* x;
+    const float* y;
+    const float* tx;
+    const float* ty;
+    const uint8_t* flags;
+    const uint32_t* trk_off;  /* E + 1 entries */
+} velo_tracks;
+
+/* Compass parameters (Sec. V: sectors searched and candidates tested; the
+ * tolerances are this library's, the paper gives none). */
+typedef struct compass_params {
+    int n_sectors;          /* 1..5 sectors per layer: central, then c-1, c+1, c-2, c+2 */
+    int n_candidates;       /* >= 1 valid tracklets tested per track          */
+    float qop_max;          /* largest |q/p| searched (1/GeV)                 */
+    float tol_win;          /* window half-width = kick_k*qop_max*|z-z_kink| + tol_win */
+    float tol_kink;         /* pair line residual at z_kink                   */
+    float tol_col;          /* collection distance in layers 2 and 4          */
+    float tol_slope;        /* pair residual slope <= kick_k*qop_max + tol_slope */
+    float chi2ndof_max;     /* chi2/(nhits-1) cut                             */
+    float sigma_hit;        /* hit resolution (mm)                            */
+    float sigma_x_prior;    /* VELO x prior (mm), > 0                         */
+    float sigma_tx_prior;   /* VELO tx prior, > 0                             */
+    float z_kink;           /* kink plane of the magnet kick (mm)             */
+    float kick_k;           /* kick: dx = kick_k*(q/p)*(z - z_kink)           */
+} compass_params;
+
+/* One output slot per VELO track (Sec. V-B output, placed at the track's
+ * own index instead of an atomic counter, so results are deterministic). */
+typedef struct compass_tracks {
+    int32_t* hit;           /* [T][4] global hit index per layer, -1 = none  */
+    float* qop;             /* fitted q/p (1/GeV); charge = sign             */
+    float* chi2;            /* fit chi2 (ndof = nhits - 1)                   */
+    float* x;               /* fitted x at z_velo                            */
+    float* tx;              /* fitted tx                                     */
+    uint8_t* nhits;         /* 0, 3 or 4                                     */
+    uint8_t* found;         /* 1 if a tracklet was selected                  */
+} compass_tracks;
+
+typedef struct ut_ctx ut_ctx;
+
+/* Create a context on the current device: copies the geometry and
+ * allocates the device status word.  Returns UT_ERR_ARG for a bad geometry
+ * (n_sectors < 1 or > 4096, strips < 1 or > 512, non-positive pitches). */
+int ut_ctx_create(ut_ctx** ctx, const ut_geometry* geom);
+int ut_ctx_destroy(ut_ctx* ctx);
+
+/* Synchronise `stream`, then report the recorded device error (0 if none):
+ * *code = UT_ERR_*, *where_a = event (-1 if global), *where_b = bank or
+ * track index within the event (-1 if global).  Does not clear it. */
+int ut_status(ut_ctx* ctx, void* stream, int* code, int64_t* where_a, int64_t* where_b);
+/* Enqueue a reset of the status word on `stream`. */
+int ut_status_reset(ut_ctx* ctx, void* stream);
+
+/* Bytes of device scratch that ut_decode needs for n_events (the
+ * single-pass prefix sum's per-event look-back state and a work counter). */
+size_t ut_decode_workspace_size(int n_events);
+
+/*
+ * ut_decode -- raw banks to hits (Sec. IV, Table I: hit counting, prefix
+ * sum, pre-decode, permutation, gather), in one single-pass kernel.
+ *
+ * d_raw:     u32 raw words of the batch, n_raw_words of them; 16-byte
+ *            aligned, and the allocation must hold n_raw_words rounded up to
+ *            a multiple of 4 words (events are read in 16-byte units).
+ * d_ev_off:  u64[n_events + 1] word offset of each event in d_raw
+ *            (non-decreasing, last <= n_raw_words; an event that breaks
+ *            this is reported as UT_ERR_DIR at its bank 0).
+ * n_events:  >= 0.  n_events == 0 writes hit_off[0] = 0.
+ * out:       hit arrays (capacity entries) and hit_off (n_events*B + 1).
+ * sorted:    1 = hits of each bank stably ordered by half-strip (= by x);
+ *            0 = bank order, word order inside a bank.
+ * d_workspace / workspace_bytes: >= ut_decode_workspace_size(n_events)
+ *            bytes of caller-owned device scratch, 16-byte aligned; the
+ *            call clears it on `stream` before use.
+ * Raw-data errors (UT_ERR_DIR, _HEADER, _STRIP) and UT_ERR_CAPACITY are
+ * recorded in the status word.
+ */
+int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, const uint64_t* d_ev_off,
+              int n_events, ut_hits* out, int sorted, void* d_workspace, size_t workspace_bytes,
+              void* stream);
+
+/*
+ * ut_sort_hits -- the permutation + gather steps of Table I as a separate
+ * pass: every bank of `in` (same hit_off layout) is stably sorted by
+ * half-strip into `out` (out->hit_off is not written; it equals
+ * in->hit_off).  d_perm (nullable): u32[total] with d_perm[i] = input
+ * position of output position i.  in and out must not overlap.
+ */
+int ut_sort_hits(ut_ctx* ctx, const ut_hits* in, ut_hits* out, uint32_t* d_perm, int n_events,
+                 void* stream);
+
+/*
+ * compass_find -- window search (Sec. V-A) and tracklet finding with the
+ * closed-form fit and best-candidate selection (Sec. V-B) for every VELO
+ * track of the batch.  `hits` must be sorted (ut_decode sorted=1 or
+ * ut_sort_hits).  n_tracks = velo trk_off[n_events].
+ * d_win (nullable): int16 [n_tracks][4][n_sectors][2] windows as (first hit
+ * relative to the event's layer start, size), (-1, -1) when empty;
+ * UT_ERR_WIN16 is recorded if a value does not fit.
+ * Launch shape: `tracks_per_warp` in {1, 2, 4} (0 = default 1) and
+ * `block` threads in {64..1024, multiple of 32} (0 = default 256).
+ */
+int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int n_events,
+                 uint32_t n_tracks, const compass_params* p, compass_tracks* out,
+                 int16_t* d_win, int tracks_per_warp, int block, void* stream);
+
+/*
+ * compass_fit -- the closed-form p-kick least-squares fit (Sec. III-C,
+ * Sec. V-B) of the hits given in out->hit for n_tracks tracks whose VELO
+ * states are velo->x[0..n_tracks) (trk_off unused).  Writes qop, chi2, x,
+ * tx; tracks with fewer than 3 hits (or a failed solve) get qop = chi2 = 0,
+ * x = VELO x, tx = VELO tx.  nhits and found are not touched.
+ */
+int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint32_t n_tracks,
+                const compass_params* p, compass_tracks* inout, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UT_COMPASS_H */

@@ -57,7 +57,7 @@ def lib():
             _lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             _lib.orc_decode.restype = ctypes.c_int
-            _lib.orc_decode.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_float,
+            _lib.orc_decode.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                         ctypes.c_uint64, P, P, P, P, P, P, P, P, ctypes.c_int]
             _lib.orc_sort_hits.restype = ctypes.c_int
@@ -127,7 +127,7 @@ def params_struct(p) -> _Params:
 
 
 def decode(raw, ev_off, n_events, geom, sorted_=True, capacity=None, n_threads=0,
-           raise_on_error=True):
+           raise_on_error=True, n_words=None):
     """Decode a batch's raw banks (Sec. IV).  Returns (code, Hits, (event, bank))."""
     raw = np.ascontiguousarray(raw, dtype=np.uint32)
     ev_off = np.ascontiguousarray(ev_off, dtype=np.uint64)
@@ -144,7 +144,8 @@ def decode(raw, ev_off, n_events, geom, sorted_=True, capacity=None, n_threads=0
     ee = np.zeros(1, np.int64)
     eb = np.zeros(1, np.int64)
     zl = np.ascontiguousarray(geom.z, dtype=np.float32)
-    rc = lib().orc_decode(_p(raw), _p(ev_off), n_events, geom.n_sectors, _p(zl),
+    nwords = raw.size if n_words is None else int(n_words)
+    rc = lib().orc_decode(_p(raw), nwords, _p(ev_off), n_events, geom.n_sectors, _p(zl),
                           geom.sector_pitch, geom.strip_pitch, geom.strips, geom.x_min,
                           1 if sorted_ else 0, int(capacity), _p(x), _p(z), _p(sector),
                           _p(layer), _p(hid), _p(hit_off), _p(ee), _p(eb), n_threads)

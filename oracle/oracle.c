@@ -109,12 +109,13 @@ static float hit_x(int s, int h, float sector_pitch, float strip_pitch, float x_
 }
 
 /*
- * raw/ev_off: the batch; E events, S sectors per layer (B = 4S banks).
+ * raw/ev_off: the batch (n_words u32 words); E events, S sectors per layer
+ * (B = 4S banks).  An event outside the buffer is a DIR error at bank 0.
  * z[4]: layer z.  sorted != 0: hits of each bank ordered by (h, word index).
  * Outputs (capacity entries each): x, zh, sector, layer, id; hit_off[E*B+1].
  * err_event/err_bank: where the reported error is (-1 for capacity).
  */
-int orc_decode(const uint32_t* raw, const uint64_t* ev_off, int E, int S,
+int orc_decode(const uint32_t* raw, uint64_t n_words, const uint64_t* ev_off, int E, int S,
                const float* z, float sector_pitch, float strip_pitch, int strips, float x_min,
                int sorted, uint64_t capacity,
                float* x, float* zh, uint16_t* sector, uint8_t* layer, uint32_t* id,
@@ -131,9 +132,13 @@ int orc_decode(const uint32_t* raw, const uint64_t* ev_off, int E, int S,
     /* Pass 1: hit counts per bank ("calculate number of hits"). */
 #pragma omp parallel for schedule(dynamic, 4)
     for (int e = 0; e < E; ++e) {
+        /* an event must lie inside the buffer and hold its directory */
+        if (ev_off[e + 1] < ev_off[e] || ev_off[e + 1] > n_words ||
+            ev_off[e + 1] - ev_off[e] < (uint64_t)B) {
+            ev_err[e] = ORC_ERR_DIR; ev_err_bank[e] = 0; continue;
+        }
         const uint32_t* ev = raw + ev_off[e];
         uint64_t nw = ev_off[e + 1] - ev_off[e];
-        if (nw < (uint64_t)B) { ev_err[e] = ORC_ERR_DIR; ev_err_bank[e] = 0; continue; }
         for (int b = 0; b < B; ++b) {
             uint32_t n = 0;
             int rc = check_bank(ev, nw, B, b, strips, &n);
@@ -474,7 +479,7 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             double m0 = margin(u[0], (double)g->x_min), m1 = margin(u[0], x_max);
             if (m0 < mm) mm = m0;
             if (m1 < mm) mm = m1;
-            if (u[0] < (double)g->x_min || u[0] > x_max) { near_m[tr] = mm; continue; }
+            if (!(u[0] >= (double)g->x_min && u[0] <= x_max)) { near_m[tr] = mm; continue; }
 
             /* Windows (Sec. V-A): central sector, then neighbours. */
             int any = 0;
@@ -484,9 +489,8 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
                 double fq = floor(q);
                 double mq = margin(q, fq) < margin(q, fq + 1.0) ? margin(q, fq) : margin(q, fq + 1.0);
                 if (mq < mm) mm = mq;
-                int c = (int)fq;
-                if (c < 0) c = 0;
-                if (c > S - 1) c = S - 1;
+                /* clamp to the plane's sectors before the integer conversion */
+                int c = (int)fmin(fmax(fq, 0.0), (double)(S - 1));
                 uint32_t layer_start = hit_off[(size_t)e * B + (size_t)l * S];
                 for (int k = 0; k < nsec; ++k) {
                     int s = c + slot_off[k];

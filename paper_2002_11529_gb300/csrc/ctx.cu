@@ -1,0 +1,67 @@
+// Context: geometry copy, device status word, status read-back.
+#include <new>
+
+#include "common.cuh"
+
+using namespace utc;
+
+extern "C" int ut_ctx_create(ut_ctx** out, const ut_geometry* geom) {
+    if (!out || !geom) return UT_ERR_ARG;
+    *out = nullptr;
+    const ut_geometry& g = *geom;
+    if (g.n_sectors < 1 || g.n_sectors > 4096 || g.strips < 1 || g.strips > 512 || !(g.sector_pitch > 0.f) ||
+        !(g.strip_pitch > 0.f))
+        return UT_ERR_ARG;
+    ut_ctx* c = new (std::nothrow) ut_ctx();
+    if (!c) return UT_ERR_ARG;
+    c->geom = g;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(unsigned long long)) != cudaSuccess) {
+        delete c;
+        return UT_ERR_CUDA;
+    }
+    if (cudaMallocHost(&c->h_status, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0xFF, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return UT_ERR_CUDA;
+    }
+    *out = c;
+    return UT_OK;
+}
+
+extern "C" int ut_ctx_destroy(ut_ctx* c) {
+    if (!c) return UT_ERR_ARG;
+    cudaFree(c->d_status);
+    cudaFreeHost(c->h_status);
+    delete c;
+    return UT_OK;
+}
+
+extern "C" int ut_status_reset(ut_ctx* c, void* stream) {
+    if (!c) return UT_ERR_ARG;
+    return check_cuda(cudaMemsetAsync(c->d_status, 0xFF, sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
+}
+
+extern "C" int ut_status(ut_ctx* c, void* stream, int* code, int64_t* where_a, int64_t* where_b) {
+    if (!c || !code) return UT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return UT_ERR_CUDA;
+    const unsigned long long k = *c->h_status;
+    if (k == ~0ull) {
+        *code = UT_OK;
+        if (where_a) *where_a = -1;
+        if (where_b) *where_b = -1;
+        return UT_OK;
+    }
+    *code = -(int)(k & 0xFF);
+    const unsigned long long a = k >> 32, b = (k >> 8) & 0xFFFFFF;
+    if (where_a) *where_a = a == 0xFFFFFFFFull ? -1 : (int64_t)a;
+    if (where_b) *where_b = b == 0xFFFFFFull ? -1 : (int64_t)b;
+    return UT_OK;
+}
