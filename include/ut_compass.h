@@ -160,6 +160,37 @@ int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, const ui
               void* stream);
 
 /*
+ * ut_decode_noalloc -- ut_decode for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this entry point exists for
+ * host frameworks that reserve all device memory for their own pool at
+ * start-up and hand out only fixed buffers, or that must not pay the
+ * implicit synchronisation of cudaMalloc on their processing path.  Such a
+ * caller cannot provide ut_decode's workspace or create a ut_ctx (which
+ * allocates its status word).
+ *
+ * Same decoding and outputs as ut_decode (same kernel).  Differences:
+ *   - no ut_ctx: the geometry is passed directly (validated as in
+ *     ut_ctx_create);
+ *   - no workspace: the scratch is a file-scope device array of the
+ *     library, sized for at most 65536 events (16 + 8*65536 bytes, held on
+ *     every GPU that loads the library until the process exits);
+ *     n_events > 65536 returns UT_ERR_ARG;
+ *   - d_status: caller-owned device u64 that receives the error key; the
+ *     call sets it to "no error" on `stream` first.  Decode it as ut_status
+ *     does: all ones = no error, else code = -(key & 0xFF), event =
+ *     key >> 32, bank = (key >> 8) & 0xFFFFFF (all ones = -1).
+ * Nothing is allocated: no cudaMalloc/cudaFree.  The first call on a device
+ * looks up the array's device address with that device current (call it
+ * once before any stream capture).  Every call on a device shares the one
+ * array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  The call clears the part of the
+ * array it uses before the kernel runs.
+ */
+int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw, uint64_t n_raw_words,
+                      const uint64_t* d_ev_off, int n_events, ut_hits* out, int sorted,
+                      unsigned long long* d_status, void* stream);
+
+/*
  * ut_sort_hits -- the permutation + gather steps of Table I as a separate
  * pass: every bank of `in` (same hit_off layout) is stably sorted by
  * half-strip into `out` (out->hit_off is not written; it equals

@@ -24,7 +24,8 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPA
              -6: "WIN16", -7: "TIMEOUT", -8: "CUDA"}
 
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_status", "ut_status_reset",
-           "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit")
+           "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
+           "ut_decode_noalloc")
 
 
 class UtGeometry(ctypes.Structure):
@@ -83,6 +84,7 @@ def lib():
                 "ut_sort_hits": ([P, P, P, P, I, P], I),
                 "compass_find": ([P, P, P, I, U32, P, P, P, I, I, P], I),
                 "compass_fit": ([P, P, P, U32, P, P, P], I),
+                "ut_decode_noalloc": ([P, P, U64, P, I, P, I, P, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -264,6 +266,27 @@ def ut_decode(ctx, raw, n_raw_words, ev_off, n_events, out: HitBuffers, sorted_=
                          workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "ut_decode")
     return workspace
+
+
+def ut_decode_noalloc(geom, raw, n_raw_words, ev_off, n_events, out: HitBuffers, status,
+                      sorted_=True, stream=None):
+    """ut_decode without allocations: scratch in the library's static device
+    array, errors in `status` (int64 device tensor of one element)."""
+    g = geometry_struct(geom)
+    h = out.struct()
+    rc = lib().ut_decode_noalloc(ctypes.byref(g), _ptr(raw), int(n_raw_words), _ptr(ev_off),
+                                 int(n_events), ctypes.byref(h), 1 if sorted_ else 0, _ptr(status),
+                                 _stream(stream))
+    _check(rc, "ut_decode_noalloc")
+
+
+def decode_status_key(key: int):
+    """(code, event, bank) of a status key (all ones = no error)."""
+    key &= 0xFFFFFFFFFFFFFFFF
+    if key == 0xFFFFFFFFFFFFFFFF:
+        return UT_OK, -1, -1
+    a, b = key >> 32, (key >> 8) & 0xFFFFFF
+    return -(key & 0xFF), (-1 if a == 0xFFFFFFFF else a), (-1 if b == 0xFFFFFF else b)
 
 
 def ut_sort_hits(ctx, hits_in: HitBuffers, hits_out: HitBuffers, n_events, perm=None, stream=None):

@@ -12,6 +12,9 @@
 // Every byte of raw input is read from HBM once; every hit is written once
 // (15 bytes of SoA + 4 bytes of offset per bank).
 
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 
 namespace utc {
@@ -523,5 +526,99 @@ extern "C" int ut_sort_hits(ut_ctx* ctx, const ut_hits* in, ut_hits* out, uint32
     if (cudaFuncSetAttribute(ut_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
     ut_sort_kernel<<<n_events, kDecodeThreads, smem, st>>>(a);
+    return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// ut_decode_noalloc: the same decode kernel for callers that cannot allocate
+// device memory.  Its scratch (the look-back state and the work counter) lives
+// in this file-scope device array instead of a caller-provided workspace.
+// Every GPU that loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace utc {
+
+constexpr int kNoAllocMaxEvents = 65536;
+constexpr size_t kNoAllocScratchBytes = 16 + (size_t)kNoAllocMaxEvents * sizeof(unsigned long long);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// In host code `g_noalloc_scratch` is only a stand-in symbol, not a device
+// address: its device address is looked up once per device, with that
+// device current, and cached.
+static std::mutex g_noalloc_mutex;
+static std::unordered_map<int, void*> g_noalloc_addr;
+
+static int noalloc_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return UT_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return UT_OK;
+    }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return UT_ERR_CUDA;
+    g_noalloc_addr.emplace(dev, p);
+    *out = p;
+    return UT_OK;
+}
+
+}  // namespace utc
+
+extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw, uint64_t n_raw_words,
+                                 const uint64_t* d_ev_off, int n_events, ut_hits* out, int sorted,
+                                 unsigned long long* d_status, void* stream) {
+    if (!geom || !out || !out->hit_off || !d_status) return UT_ERR_ARG;
+    if (n_events < 0 || n_events > kNoAllocMaxEvents) return UT_ERR_ARG;
+    const ut_geometry& g = *geom;
+    if (g.n_sectors < 1 || g.n_sectors > 4096 || g.strips < 1 || g.strips > 512 || !(g.sector_pitch > 0.f) ||
+        !(g.strip_pitch > 0.f))
+        return UT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != UT_OK) return rc;
+    if (cudaMemsetAsync(d_status, 0xFF, sizeof(unsigned long long), st) != cudaSuccess) return UT_ERR_CUDA;
+    if (n_events == 0) return check_cuda(cudaMemsetAsync(out->hit_off, 0, sizeof(uint32_t), st));
+    if (!d_raw || !d_ev_off || !out->x || !out->z || !out->sector || !out->layer || !out->id) return UT_ERR_ARG;
+    if (((uintptr_t)d_raw & 15u) != 0) return UT_ERR_ARG;
+    const int S = g.n_sectors, B = 4 * S;
+    DecodeArgs a;
+    a.raw = d_raw;
+    a.n_words = n_raw_words;
+    a.ev_off = d_ev_off;
+    a.n_events = n_events;
+    a.S = S;
+    a.x = out->x;
+    a.z = out->z;
+    a.sector = out->sector;
+    a.layer = out->layer;
+    a.id = out->id;
+    a.hit_off = out->hit_off;
+    a.capacity = out->capacity;
+    a.x_min = g.x_min;
+    a.sector_pitch = g.sector_pitch;
+    a.half_pitch = g.strip_pitch * 0.5f;
+    a.strips = g.strips;
+    for (int l = 0; l < 4; ++l) a.zl[l] = g.z[l];
+    a.ticket = static_cast<unsigned int*>(scratch);
+    a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 16);
+    a.status = d_status;
+    a.stage_words = kStageWordsDefault;
+    // the array keeps the previous call's contents: clear the counter and the
+    // look-back state of the events used here
+    if (cudaMemsetAsync(scratch, 0, 16 + (size_t)n_events * sizeof(unsigned long long), st) != cudaSuccess)
+        return UT_ERR_CUDA;
+    const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words);
+    cudaError_t err;
+    if (sorted) {
+        err = cudaFuncSetAttribute(ut_decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) ut_decode_kernel<true><<<n_events, kDecodeThreads, smem, st>>>(a);
+    } else {
+        err = cudaFuncSetAttribute(ut_decode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) ut_decode_kernel<false><<<n_events, kDecodeThreads, smem, st>>>(a);
+    }
+    if (err != cudaSuccess) return UT_ERR_CUDA;
     return check_cuda(cudaGetLastError());
 }
