@@ -55,6 +55,7 @@ struct FindArgs {
     uint8_t* found;
     int16_t* win;
     unsigned long long* status;
+    int stage_cap;               // staged residuals per layer and track
 };
 
 // Track prediction in the measured coordinate of layer l:
@@ -132,89 +133,128 @@ __device__ __forceinline__ bool fit32(const float* d, const bool* present, const
     return true;
 }
 
-// Per-group shared state.
-template <int CAP>
-struct GroupSmem {
-    float d[4][CAP];
-    int idx[4][CAP];
-    int wfirst[4][kMaxSectors];
+// Per-group shared state: window descriptors and the staged residuals of
+// the contiguous hit range of the searched sectors of every layer.
+struct GroupHead {
+    int wfirst[4][kMaxSectors];  // window start, position within the layer range
     int wsize[4][kMaxSectors];
+    int base[4];                 // global index of the layer range's first hit
+    int len[4];                  // hits in the layer range
+    int wunion[4][2];            // [first, end) of all windows of the layer
 };
 
-// Residual and global index of combined-range position i of layer l.
-template <int CAP>
-struct Ranges {
-    const GroupSmem<CAP>* sm;
+struct View {
+    const GroupHead* h;
+    const float* sd;             // [4][cap]
     const float* hx;
+    int cap;
     float hi[4], lo[4];
-    int n[4];
-    int n_sec;
 
-    __device__ __forceinline__ int index(int l, int i) const {
-        if (i < CAP) return sm->idx[l][i];
-        int pre = 0;
-        for (int k = 0; k < n_sec; ++k) {
-            const int sz = sm->wsize[l][k];
-            if (i < pre + sz) return sm->wfirst[l][k] + (i - pre);
-            pre += sz;
-        }
-        return -1;
+    // residual of range position pos of layer l
+    __device__ __forceinline__ float d(int l, int pos) const {
+        if (pos < cap) return sd[l * cap + pos];
+        return (__ldg(hx + h->base[l] + pos) - hi[l]) - lo[l];
     }
-    __device__ __forceinline__ float d(int l, int i) const {
-        if (i < CAP) return sm->d[l][i];
-        return (__ldg(hx + index(l, i)) - hi[l]) - lo[l];
+    // first position in [a, b) with d >= v (d is non-decreasing there)
+    __device__ __forceinline__ int lower(int l, int a, int b, float v) const {
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (d(l, m) >= v) b = m; else a = m + 1;
+        }
+        return a;
     }
 };
 
 struct Tracklet {
     int nh;
     float chi2, a, b, q;
-    int hits[4];
+    int pos[4];                  // range positions, -1 = none
 };
 
-// Pair (ia, ib) of direction dir: cuts, collection, fit (Sec. V-B).
-// Returns true for a valid tracklet.
-template <int CAP>
-__device__ __forceinline__ bool eval_pair(const FindArgs& A, const Ranges<CAP>& R, int dir, int ia, int ib,
+// Hits of layer l's combined range (all windows) whose residual lies in
+// [lo, hi] are the range positions [p0, p1): the staged range is sorted by
+// x over all its sectors, so one pair of binary searches finds them.  The
+// caller visits them slot by slot (combined-range order).
+__device__ __forceinline__ void band(const View& V, int l, int w0, int w1, float lo, float hi, int& p0, int& p1) {
+    p0 = V.lower(l, w0, w1, lo);
+    int a = p0, b = w1;
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (V.d(l, m) > hi) b = m; else a = m + 1;
+    }
+    p1 = a;
+}
+
+// Collection in layer l (Sec. V-B): the hit nearest `pred` within tol_col,
+// ties to the earliest in combined-range order (slot order, then position).
+// Only hits inside [pred - tol_col - m, pred + tol_col + m] can qualify; the
+// exact float test decides.
+__device__ __forceinline__ int collect(const FindArgs& A, const View& V, int l, float pred, float& dsel) {
+    const float m = 1e-5f * (1.f + fabsf(pred) + A.tol_col);
+    int p0, p1;
+    band(V, l, V.h->wunion[l][0], V.h->wunion[l][1], pred - A.tol_col - m, pred + A.tol_col + m, p0, p1);
+    int bi = -1;
+    if (p0 >= p1) return bi;
+    float bd = 0.f;
+    for (int k = 0; k < A.n_sec; ++k) {
+        const int f = max(V.h->wfirst[l][k], p0);
+        const int e = min(V.h->wfirst[l][k] + V.h->wsize[l][k], p1);
+        for (int pos = f; pos < e; ++pos) {
+            const float dv = V.d(l, pos);
+            const float dist = fabsf(dv - pred);
+            if (!(dist <= A.tol_col)) continue;
+            if (bi < 0 || dist < bd) {
+                bi = pos;
+                bd = dist;
+                dsel = dv;
+            }
+        }
+    }
+    return bi;
+}
+
+// Exact evaluation of the anchor pair (pos_a, pos_b) of direction DIR:
+// pair cuts, collection, fit, chi2 cut (Sec. V-B).
+template <int DIR>
+__device__ __forceinline__ bool eval_pair(const FindArgs& A, const View& V, int pos_a, int pos_b, float da, float db,
                                           Tracklet& out) {
-    const int la = dir ? 3 : 0, lb = dir ? 1 : 2;
-    const int lc0 = dir ? 2 : 1, lc1 = dir ? 0 : 3;
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    constexpr int lc0 = DIR ? 2 : 1, lc1 = DIR ? 0 : 3;
     const float dzab = A.z[lb] - A.z[la];
     const float dzk = A.z_kink - A.z[la];
-    const float da = R.d(la, ia);
-    const float db = R.d(lb, ib);
     const float sr = (db - da) / dzab;
     if (!(fabsf(sr) <= A.slope_tol)) return false;
     const float dk = da + sr * dzk;
     if (!(fabsf(dk) <= A.tol_kink)) return false;
     float dl[4] = {0.f, 0.f, 0.f, 0.f};
     bool present[4] = {false, false, false, false};
-    int sel[4] = {-1, -1, -1, -1};
+    out.pos[0] = out.pos[1] = out.pos[2] = out.pos[3] = -1;
     dl[la] = da;
     present[la] = true;
-    sel[la] = ia;
+    out.pos[la] = pos_a;
     dl[lb] = db;
     present[lb] = true;
-    sel[lb] = ib;
+    out.pos[lb] = pos_b;
     int nh = 2;
-#pragma unroll
-    for (int ci = 0; ci < 2; ++ci) {
-        const int l = ci ? lc1 : lc0;
-        const float pred = da + sr * (A.z[l] - A.z[la]);
-        int bi = -1;
-        float bd = 0.f;
-        for (int j = 0; j < R.n[l]; ++j) {
-            const float dist = fabsf(R.d(l, j) - pred);
-            if (!(dist <= A.tol_col)) continue;
-            if (bi < 0 || dist < bd) {
-                bi = j;
-                bd = dist;
-            }
-        }
+    {
+        const float pred = da + sr * (A.z[lc0] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = collect(A, V, lc0, pred, dsel);
         if (bi >= 0) {
-            dl[l] = R.d(l, bi);
-            present[l] = true;
-            sel[l] = bi;
+            dl[lc0] = dsel;
+            present[lc0] = true;
+            out.pos[lc0] = bi;
+            ++nh;
+        }
+    }
+    {
+        const float pred = da + sr * (A.z[lc1] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = collect(A, V, lc1, pred, dsel);
+        if (bi >= 0) {
+            dl[lc1] = dsel;
+            present[lc1] = true;
+            out.pos[lc1] = bi;
             ++nh;
         }
     }
@@ -228,13 +268,131 @@ __device__ __forceinline__ bool eval_pair(const FindArgs& A, const Ranges<CAP>& 
     out.a = fa;
     out.b = fb;
     out.q = fq;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) out.hits[l] = sel[l] >= 0 ? R.index(l, sel[l]) : -1;
     return true;
 }
 
-template <int G, int CAP>
-__global__ void __launch_bounds__(256) compass_find_kernel(const FindArgs A) {
+// Range position of combined-range index i of layer l (slot walk).
+__device__ __forceinline__ int slot_pos(const GroupHead* h, int l, int n_sec, int i) {
+    int pre = 0;
+    for (int k = 0; k < n_sec; ++k) {
+        const int sz = h->wsize[l][k];
+        if (i < pre + sz) return h->wfirst[l][k] + (i - pre);
+        pre += sz;
+    }
+    return -1;
+}
+
+// All valid tracklets whose first anchor is combined index ia, in order;
+// returns how many (at most `limit`) and the best of them (strictly better
+// replaces, so the earliest wins ties).
+template <int DIR>
+__device__ __forceinline__ int scan_anchor(const FindArgs& A, const View& V, int ia, int limit, int& best_nh,
+                                           float& best_c2, int& best_pa, int& best_pb) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const int pos_a = slot_pos(V.h, la, A.n_sec, ia);
+    const float da = V.d(la, pos_a);
+    // Band of d_b that can pass the kink cut: |da (1 - r) + db r| <= tol_kink
+    // with r = (z_kink - z_a)/(z_b - z_a), widened far beyond float rounding.
+    const float r = (A.z_kink - A.z[la]) / (A.z[lb] - A.z[la]);
+    float blo = -INFINITY, bhi = INFINITY;
+    if (fabsf(r) > 1e-3f) {
+        const float mag = (1.f + fabsf(da) + A.hw[lb]) * (1.f + fabsf(r));
+        const float eps = 1e-5f * mag;
+        const float c = da * (1.f - r);
+        float e0 = (-A.tol_kink - eps - c) / r, e1 = (A.tol_kink + eps - c) / r;
+        if (e0 > e1) {
+            const float t = e0;
+            e0 = e1;
+            e1 = t;
+        }
+        blo = e0 - 1e-5f * (1.f + fabsf(e0));
+        bhi = e1 + 1e-5f * (1.f + fabsf(e1));
+    }
+    int p0, p1;
+    band(V, lb, V.h->wunion[lb][0], V.h->wunion[lb][1], blo, bhi, p0, p1);
+    int nvalid = 0;
+    if (p0 >= p1) return 0;
+    for (int k = 0; k < A.n_sec && nvalid < limit; ++k) {
+        const int f = max(V.h->wfirst[lb][k], p0);
+        const int e = min(V.h->wfirst[lb][k] + V.h->wsize[lb][k], p1);
+        for (int pos_b = f; pos_b < e; ++pos_b) {
+            const float db = V.d(lb, pos_b);
+            Tracklet tk;
+            if (!eval_pair<DIR>(A, V, pos_a, pos_b, da, db, tk)) continue;
+            ++nvalid;
+            if (tk.nh > best_nh || (tk.nh == best_nh && tk.chi2 < best_c2)) {
+                best_nh = tk.nh;
+                best_c2 = tk.chi2;
+                best_pa = pos_a;
+                best_pb = pos_b;
+            }
+            if (nvalid >= limit) break;
+        }
+    }
+    return nvalid;
+}
+
+// One direction of the tracklet search for a lane group: lanes take
+// consecutive first anchors; a prefix count over lanes keeps exactly the
+// first n_candidates valid tracklets of the sequential order.
+template <int G, int DIR>
+__device__ __forceinline__ void search_dir(const FindArgs& A, const View& V, int na, int gl, uint32_t gmask,
+                                           int& best_nh, float& best_c2, int& best_dir, int& best_pa, int& best_pb) {
+    int count = 0;
+    for (int ia0 = 0; ia0 < na && count < A.n_cand; ia0 += G) {
+        const int ia = ia0 + gl;
+        const int rem = A.n_cand - count;
+        int l_nh = 0, l_pa = -1, l_pb = -1;
+        float l_c2 = 0.f;
+        int nvalid = 0;
+        if (ia < na) nvalid = scan_anchor<DIR>(A, V, ia, rem, l_nh, l_c2, l_pa, l_pb);
+        int incl = nvalid;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const int v = __shfl_up_sync(gmask, incl, o, G);
+            if (gl >= o) incl += v;
+        }
+        const int total = __shfl_sync(gmask, incl, G - 1, G);
+        if (total == 0) continue;
+        const int prefix = incl - nvalid;
+        const int limit = max(0, min(rem - prefix, nvalid));
+        if (limit == 0) {
+            l_nh = 0;
+        } else if (limit < nvalid) {
+            l_nh = 0;
+            l_c2 = 0.f;
+            scan_anchor<DIR>(A, V, ia, limit, l_nh, l_c2, l_pa, l_pb);
+        }
+        // best over lanes: most hits, lowest chi2, lowest lane (= earliest)
+        int k_nh = l_nh, k_lane = gl;
+        float k_c2 = l_c2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const int o_nh = __shfl_xor_sync(gmask, k_nh, o, G);
+            const float o_c2 = __shfl_xor_sync(gmask, k_c2, o, G);
+            const int o_lane = __shfl_xor_sync(gmask, k_lane, o, G);
+            const bool better = o_nh > k_nh || (o_nh == k_nh && (o_c2 < k_c2 || (o_c2 == k_c2 && o_lane < k_lane)));
+            if (better) {
+                k_nh = o_nh;
+                k_c2 = o_c2;
+                k_lane = o_lane;
+            }
+        }
+        const int w_pa = __shfl_sync(gmask, l_pa, k_lane, G);
+        const int w_pb = __shfl_sync(gmask, l_pb, k_lane, G);
+        if (k_nh > best_nh || (k_nh == best_nh && k_nh > 0 && k_c2 < best_c2)) {
+            best_nh = k_nh;
+            best_c2 = k_c2;
+            best_dir = DIR;
+            best_pa = w_pa;
+            best_pb = w_pb;
+        }
+        count += min(total, rem);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256, 2) compass_find_kernel(const FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gpb = blockDim.x / G;
     const int g = threadIdx.x / G;
@@ -243,7 +401,10 @@ __global__ void __launch_bounds__(256) compass_find_kernel(const FindArgs A) {
     const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const uint32_t t = blockIdx.x * (uint32_t)gpb + (uint32_t)g;
     if (t >= A.n_tracks) return;
-    GroupSmem<CAP>* sm = reinterpret_cast<GroupSmem<CAP>*>(smem_raw) + g;
+    const int cap = A.stage_cap;
+    const size_t stride = sizeof(GroupHead) + (size_t)4 * cap * sizeof(float);
+    GroupHead* head = reinterpret_cast<GroupHead*>(smem_raw + (size_t)g * stride);
+    float* sd = reinterpret_cast<float*>(smem_raw + (size_t)g * stride + sizeof(GroupHead));
 
     // Event of the track: largest e with trk_off[e] <= t.
     int lo = 0, hi = A.n_events;
@@ -253,66 +414,99 @@ __global__ void __launch_bounds__(256) compass_find_kernel(const FindArgs A) {
     }
     const int e = lo;
     const int B = 4 * A.S;
+    const int n_sec = A.n_sec;
     const float vx = A.vx[t], vy = A.vy[t], vtx = A.vtx[t], vty = A.vty[t];
     const bool backward = (A.vflags[t] & 1u) != 0;
 
-    // Extrapolation: lane l computes layer l, then every lane gets all four.
+    // Extrapolation (Sec. V-A): lane l computes layer l.
     LayerPred mine;
     mine.hi = mine.lo = 0.f;
     mine.c = 0;
     mine.u = 0.0;
     if (gl < 4) mine = predict(A, vx, vy, vtx, vty, gl);
-    Ranges<CAP> R;
-    R.sm = sm;
-    R.hx = A.hx;
-    R.n_sec = A.n_sec;
+    View V;
+    V.h = head;
+    V.sd = sd;
+    V.hx = A.hx;
+    V.cap = cap;
     int cs[4];
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        R.hi[l] = __shfl_sync(gmask, mine.hi, l, G);
-        R.lo[l] = __shfl_sync(gmask, mine.lo, l, G);
+        V.hi[l] = __shfl_sync(gmask, mine.hi, l, G);
+        V.lo[l] = __shfl_sync(gmask, mine.lo, l, G);
         cs[l] = __shfl_sync(gmask, mine.c, l, G);
     }
     const double u0 = __shfl_sync(gmask, mine.u, 0, G);
     const double x_max = (double)A.x_min + (double)A.S * (double)A.pitch;
     const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= x_max);
 
-    // Windows: lane j handles (layer j / n_sec, slot j % n_sec).
-    const int nwin = 4 * A.n_sec;
-    for (int j = gl; j < nwin; j += G) {
-        const int l = j / A.n_sec, k = j % A.n_sec;
-        // slot order: central, c-1, c+1, c-2, c+2
+    if (gl == 0) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
+        A.qop[t] = 0.f;
+        A.chi2[t] = 0.f;
+        A.xo[t] = vx;
+        A.txo[t] = vtx;
+        A.nhits[t] = 0;
+        A.found[t] = 0;
+    }
+    if (!accept) {
+        if (A.win)
+            for (int j = gl; j < 4 * n_sec * 2; j += G) A.win[(size_t)t * 4 * n_sec * 2 + j] = -1;
+        return;
+    }
+
+    // Hit range of the searched sectors of each layer (contiguous banks).
+    if (gl < 4) {
+        const int l = gl;
+        const int c = mine.c;
+        const int s0 = max(c - n_sec / 2, 0), s1 = min(c + (n_sec - 1) / 2, A.S - 1);
+        const size_t b0 = (size_t)e * B + (size_t)l * A.S;
+        const int a0 = (int)__ldg(A.hit_off + b0 + s0);
+        head->base[l] = a0;
+        head->len[l] = (int)__ldg(A.hit_off + b0 + s1 + 1) - a0;
+    }
+    __syncwarp(gmask);
+    // Stage residuals (independent loads, one round of latency).
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const int n = min(head->len[l], cap);
+        const int a0 = head->base[l];
+        for (int pos = gl; pos < n; pos += G) sd[l * cap + pos] = (__ldg(A.hx + a0 + pos) - V.hi[l]) - V.lo[l];
+    }
+    __syncwarp(gmask);
+
+    // Windows (Sec. V-A): the staged range is sorted by x, so the union of
+    // the windows of a layer is the one run of positions with |d| <= hw; the
+    // window of each slot sector is its part of that run.
+    if (gl < 4) {
+        const int l = gl;
+        const float hw = A.hw[l];
+        int w0, w1;
+        band(V, l, 0, head->len[l], -hw, hw, w0, w1);
+        head->wunion[l][0] = w0;
+        head->wunion[l][1] = w1;
+    }
+    __syncwarp(gmask);
+    for (int j = gl; j < 4 * n_sec; j += G) {
+        const int l = j / n_sec, k = j % n_sec;
         const int s = cs[l] + ((k + 1) >> 1) * ((k & 1) ? -1 : 1);
         int first = 0, size = 0;
-        if (accept && s >= 0 && s < A.S) {
+        if (s >= 0 && s < A.S) {
             const size_t bank = (size_t)e * B + (size_t)l * A.S + s;
-            const uint32_t a0 = __ldg(A.hit_off + bank), a1 = __ldg(A.hit_off + bank + 1);
-            const float hw = A.hw[l], uh = R.hi[l], ul = R.lo[l];
-            // first position with d >= -hw
-            uint32_t lo_i = a0, hi_i = a1;
-            while (lo_i < hi_i) {
-                const uint32_t mid = (lo_i + hi_i) >> 1;
-                const float dm = (__ldg(A.hx + mid) - uh) - ul;
-                if (dm >= -hw) hi_i = mid; else lo_i = mid + 1;
-            }
-            const uint32_t f0 = lo_i;
-            // first position with d > hw
-            hi_i = a1;
-            while (lo_i < hi_i) {
-                const uint32_t mid = (lo_i + hi_i) >> 1;
-                const float dm = (__ldg(A.hx + mid) - uh) - ul;
-                if (dm > hw) hi_i = mid; else lo_i = mid + 1;
-            }
-            first = (int)f0;
-            size = (int)(lo_i - f0);
+            const int a = (int)__ldg(A.hit_off + bank) - head->base[l];
+            const int b = (int)__ldg(A.hit_off + bank + 1) - head->base[l];
+            first = max(a, head->wunion[l][0]);
+            size = max(0, min(b, head->wunion[l][1]) - first);
         }
-        sm->wfirst[l][k] = first;
-        sm->wsize[l][k] = size;
+        head->wfirst[l][k] = first;
+        head->wsize[l][k] = size;
         if (A.win) {
-            int16_t* wp = A.win + (((size_t)t * 4 + l) * A.n_sec + k) * 2;
+            int16_t* wp = A.win + (((size_t)t * 4 + l) * n_sec + k) * 2;
             int16_t v0 = -1, v1 = -1;
             if (size > 0) {
-                const long long rel = (long long)first - (long long)__ldg(A.hit_off + (size_t)e * B + (size_t)l * A.S);
+                const long long rel = (long long)head->base[l] + first -
+                                      (long long)__ldg(A.hit_off + (size_t)e * B + (size_t)l * A.S);
                 if (rel > 32767 || size > 32767) {
                     report(A.status, UT_ERR_WIN16, e, (long long)(t - __ldg(A.trk_off + e)));
                 } else {
@@ -325,102 +519,30 @@ __global__ void __launch_bounds__(256) compass_find_kernel(const FindArgs A) {
         }
     }
     __syncwarp(gmask);
-
-    int any = 0;
+    int n[4], any = 0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        int n = 0;
-        for (int k = 0; k < A.n_sec; ++k) n += sm->wsize[l][k];
-        R.n[l] = n;
-        any |= n;
+        n[l] = head->wunion[l][1] - head->wunion[l][0];
+        any |= n[l];
     }
+    if (any == 0) return;
 
-    // Default (not found) output.
-    if (gl == 0) {
-#pragma unroll
-        for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
-        A.qop[t] = 0.f;
-        A.chi2[t] = 0.f;
-        A.xo[t] = vx;
-        A.txo[t] = vtx;
-        A.nhits[t] = 0;
-        A.found[t] = 0;
-    }
-    if (!accept || any == 0) return;
-
-    // Stage residuals and indices of the combined ranges.
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const int lim = min(R.n[l], CAP);
-        for (int i = gl; i < lim; i += G) {
-            int pre = 0, j = -1;
-            for (int k = 0; k < A.n_sec; ++k) {
-                const int sz = sm->wsize[l][k];
-                if (i < pre + sz) {
-                    j = sm->wfirst[l][k] + (i - pre);
-                    break;
-                }
-                pre += sz;
-            }
-            sm->idx[l][i] = j;
-            sm->d[l][i] = (__ldg(A.hx + j) - R.hi[l]) - R.lo[l];
-        }
-    }
-    __syncwarp(gmask);
-
-    // Tracklet search: forward, then backward if forward found nothing.
-    int best_nh = 0, best_dir = 0, best_p = -1;
+    // Tracklet search (Sec. V-B): forward, then backward only if forward
+    // found no valid tracklet.
+    int best_nh = 0, best_dir = 0, best_pa = -1, best_pb = -1;
     float best_c2 = 0.f;
-    const uint32_t lt = lanemask_lt() & gmask;
-    for (int dir = 0; dir < 2 && best_p < 0; ++dir) {
-        const int la = dir ? 3 : 0, lb = dir ? 1 : 2;
-        const int na = R.n[la], nb = R.n[lb];
-        const long long P = (long long)na * nb;
-        int count = 0;
-        for (long long base = 0; base < P && count < A.n_cand; base += G) {
-            const long long p = base + gl;
-            Tracklet tk;
-            bool valid = false;
-            if (p < P) {
-                const int ia = (int)(p / nb), ib = (int)(p - (long long)ia * nb);
-                valid = eval_pair<CAP>(A, R, dir, ia, ib, tk);
-            }
-            const uint32_t vmask = __ballot_sync(gmask, valid) & gmask;
-            if (vmask == 0) continue;
-            const int rank = __popc(vmask & lt);
-            const bool acc = valid && (count + rank < A.n_cand);
-            int k_nh = acc ? tk.nh : 0;
-            float k_c2 = acc ? tk.chi2 : 0.f;
-            int k_p = acc ? (int)p : INT_MAX;
-#pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) {
-                const int o_nh = __shfl_xor_sync(gmask, k_nh, off, G);
-                const float o_c2 = __shfl_xor_sync(gmask, k_c2, off, G);
-                const int o_p = __shfl_xor_sync(gmask, k_p, off, G);
-                const bool better = o_nh > k_nh || (o_nh == k_nh && (o_c2 < k_c2 || (o_c2 == k_c2 && o_p < k_p)));
-                if (better) {
-                    k_nh = o_nh;
-                    k_c2 = o_c2;
-                    k_p = o_p;
-                }
-            }
-            if (k_nh > best_nh || (k_nh == best_nh && k_nh > 0 && k_c2 < best_c2)) {
-                best_nh = k_nh;
-                best_c2 = k_c2;
-                best_p = k_p;
-                best_dir = dir;
-            }
-            count += min(__popc(vmask), A.n_cand - count);
-        }
-    }
-    if (best_p < 0 || gl != 0) return;
+    search_dir<G, 0>(A, V, n[0], gl, gmask, best_nh, best_c2, best_dir, best_pa, best_pb);
+    if (best_nh == 0) search_dir<G, 1>(A, V, n[3], gl, gmask, best_nh, best_c2, best_dir, best_pa, best_pb);
+    if (best_nh == 0 || gl != 0) return;
 
     // Re-evaluate the selected tracklet for its hits and fit.
-    const int nb = R.n[best_dir ? 1 : 2];
     Tracklet tk;
-    eval_pair<CAP>(A, R, best_dir, best_p / nb, best_p % nb, tk);
+    if (best_dir == 0)
+        eval_pair<0>(A, V, best_pa, best_pb, V.d(0, best_pa), V.d(2, best_pb), tk);
+    else
+        eval_pair<1>(A, V, best_pa, best_pb, V.d(3, best_pa), V.d(1, best_pb), tk);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.hits[l];
+    for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.pos[l] >= 0 ? head->base[l] + tk.pos[l] : -1;
     A.qop[t] = tk.q;
     A.chi2[t] = tk.chi2;
     A.xo[t] = vx + tk.a;
@@ -520,18 +642,20 @@ static int make_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* 
     A.found = out->found;
     A.win = win;
     A.status = ctx->d_status;
+    A.stage_cap = 0;
     return UT_OK;
 }
 
-template <int G, int CAP>
-static int launch_find(const FindArgs& A, int block, cudaStream_t st) {
+template <int G>
+static int launch_find(FindArgs A, int block, int stage_cap, cudaStream_t st) {
     const int gpb = block / G;
-    const size_t smem = (size_t)gpb * sizeof(GroupSmem<CAP>);
-    if (cudaFuncSetAttribute(compass_find_kernel<G, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    A.stage_cap = stage_cap;
+    const size_t smem = (size_t)gpb * (sizeof(GroupHead) + (size_t)4 * stage_cap * sizeof(float));
+    if (cudaFuncSetAttribute(compass_find_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return UT_ERR_CUDA;
     const uint32_t grid = (A.n_tracks + gpb - 1) / gpb;
-    compass_find_kernel<G, CAP><<<grid, block, smem, st>>>(A);
+    compass_find_kernel<G><<<grid, block, smem, st>>>(A);
     return check_cuda(cudaGetLastError());
 }
 
@@ -552,9 +676,9 @@ extern "C" int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
     if (block < 64 || block > 256 || block % 32 != 0) return UT_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (tracks_per_warp) {
-        case 1: return launch_find<32, 96>(A, block, st);
-        case 2: return launch_find<16, 64>(A, block, st);
-        case 4: return launch_find<8, 48>(A, block, st);
+        case 1: return launch_find<32>(A, block, 128, st);
+        case 2: return launch_find<16>(A, block, 128, st);
+        case 4: return launch_find<8>(A, block, 96, st);
         default: return UT_ERR_ARG;
     }
 }
