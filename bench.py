@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
-    ap.add_argument("--tracks-per-warp", type=int, default=1)
+    ap.add_argument("--tracks-per-warp", type=int, default=4)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

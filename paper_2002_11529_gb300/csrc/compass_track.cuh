@@ -1,0 +1,632 @@
+// Compass per-track device code (Sec. V of the paper), shared by the
+// event-centric compass_find kernel and the persistent batched kernel.
+//
+// A group of G lanes (G = 32, 16 or 8) handles one VELO track of an event
+// whose hit x (event-local positions, x-sorted inside every sector bank)
+// and bank offsets are given:
+//   1. straight extrapolation to the four layers (Sec. V-A) in double, kept
+//      as a float pair (hi, lo); hit residual d = (x - hi) - lo in float;
+//   2. windows: the searched sectors of a layer are contiguous banks and
+//      sectors tile x in order, so their hits are x-sorted as a whole and
+//      the union of the windows is the one run with |d| <= hw; the window of
+//      each slot sector is its part of that run;
+//   3. tracklet search (Sec. V-B): for each first anchor only the band of
+//      second anchors that can pass the kink cut is visited (the exact float
+//      cuts decide), collection takes the nearest hit with ties to the
+//      earliest in combined-range order, the float fit decides validity.
+//      Fast path: all valid tracklets of a direction in any order, the best
+//      by (most hits, lowest chi2, earliest); exact because when at most
+//      n_candidates tracklets are valid all of them are tested.  When more
+//      are valid, an ordered pass keeps exactly the first n_candidates of the
+//      sequential order (lanes take consecutive first anchors, a prefix
+//      count over lanes cuts at n_candidates);
+//   4. backward anchors only when the forward pass found no valid tracklet.
+// Every decision is taken in float with the operation order of the plain
+// sequential statement (built with -fmad=false).
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace utc {
+
+constexpr int kMaxSectors = 5;
+
+struct FindArgs {
+    const float* hx;
+    const uint32_t* hit_off;
+    const float* vx;
+    const float* vy;
+    const float* vtx;
+    const float* vty;
+    const uint8_t* vflags;
+    const uint32_t* trk_off;
+    int n_events;
+    uint32_t n_tracks;
+    int S;
+    float z[4], tan_a[4];
+    float x_min, pitch, z_velo;
+    int n_sec, n_cand;
+    float slope_tol, tol_kink, tol_col, chi2ndof_max, z_kink;
+    float hw[4], t[4], f[4];
+    float w, px, ptx;
+    int32_t* hit;
+    float* qop;
+    float* chi2;
+    float* xo;
+    float* txo;
+    uint8_t* nhits;
+    uint8_t* found;
+    int16_t* win;
+    unsigned long long* status;
+    float band_r[2], band_inv_r[2], band_k1[2];  // kink-band constants per direction
+    uint32_t x_cap;              // hits of an event staged in shared memory
+    int split;                   // blocks sharing one event's tracks
+};
+
+// Track prediction in the measured coordinate of layer l:
+// u_l = x_v(z_l) - y_v(z_l) * tan(a_l) in double, split into (hi, lo).
+struct LayerPred {
+    float hi, lo;
+    int c;        // central sector (clamped)
+    double u;
+};
+
+__device__ __forceinline__ LayerPred predict(const FindArgs& a, float vx, float vy, float vtx, float vty, int l) {
+    LayerPred p;
+    const double dz = (double)a.z[l] - (double)a.z_velo;
+    const double xv = (double)vx + (double)vtx * dz;
+    const double yv = (double)vy + (double)vty * dz;
+    p.u = xv - yv * (double)a.tan_a[l];
+    p.hi = (float)p.u;
+    p.lo = (float)(p.u - (double)p.hi);
+    const double q = (p.u - (double)a.x_min) / (double)a.pitch;
+    const double fq = fmin(fmax(floor(q), 0.0), (double)(a.S - 1));
+    p.c = (int)fq;
+    return p;
+}
+
+// Closed-form p-kick fit in float (Sec. III-C): residual model
+// d_l = a + b t_l + q f_l with a Gaussian prior on (a, b); LDL^T solve.
+__device__ __forceinline__ bool fit32(const float* d, const bool* present, const FindArgs& A, float& a_o,
+                                      float& b_o, float& q_o, float& chi2_o) {
+    const float w = A.w;
+    float S0 = 0.f, St = 0.f, Sf = 0.f, Stt = 0.f, Stf = 0.f, Sff = 0.f;
+    float Bd = 0.f, Btd = 0.f, Bfd = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        const float wt = w * A.t[l];
+        const float wf = w * A.f[l];
+        S0 = S0 + w;
+        St = St + wt;
+        Sf = Sf + wf;
+        Stt = Stt + wt * A.t[l];
+        Stf = Stf + wt * A.f[l];
+        Sff = Sff + wf * A.f[l];
+        Bd = Bd + w * d[l];
+        Btd = Btd + wt * d[l];
+        Bfd = Bfd + wf * d[l];
+    }
+    const float N11 = S0 + A.px, N12 = St, N13 = Sf, N22 = Stt + A.ptx, N23 = Stf, N33 = Sff;
+    const float D1 = N11;
+    const float L21 = N12 / D1;
+    const float L31 = N13 / D1;
+    const float D2 = N22 - L21 * N12;
+    const float E32 = N23 - L31 * N12;
+    const float L32 = E32 / D2;
+    const float D3 = N33 - L31 * N13 - L32 * E32;
+    if (!(D1 > 0.f) || !(D2 > 0.f) || !(D3 > 0.f)) return false;
+    const float y1 = Bd;
+    const float y2 = Btd - L21 * y1;
+    const float y3 = Bfd - L31 * y1 - L32 * y2;
+    const float z1 = y1 / D1, z2 = y2 / D2, z3 = y3 / D3;
+    const float q = z3;
+    const float b = z2 - L32 * q;
+    const float aa = z1 - L21 * b - L31 * q;
+    float chi2 = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (!present[l]) continue;
+        const float r = d[l] - aa - b * A.t[l] - q * A.f[l];
+        chi2 = chi2 + w * r * r;
+    }
+    chi2 = chi2 + A.px * aa * aa + A.ptx * b * b;
+    a_o = aa;
+    b_o = b;
+    q_o = q;
+    chi2_o = chi2;
+    return true;
+}
+
+// Per-track (lane group) shared state; positions are event-local.
+struct GroupHead {
+    int wfirst[4][kMaxSectors];  // first hit of each slot window
+    int wsize[4][kMaxSectors];
+    int pre[4][kMaxSectors];     // combined-range index of the window's first hit
+    int wunion[4][2];            // [first, end) of all windows of the layer
+    int sec0[4];                 // first searched sector
+    int cen[4];                  // central sector
+    float scale[4];              // union positions per mm (start of lower-bound walks)
+};
+
+struct View {
+    const GroupHead* h;
+    const float* X;              // event hit x (shared or global memory)
+    const uint32_t* off;         // event-local bank offsets (B + 1)
+    int S;
+    float hi[4], lo[4];
+
+    __device__ __forceinline__ float d(int l, int p) const { return (X[p] - hi[l]) - lo[l]; }
+
+    // first union position of layer l with d >= v: start at the
+    // interpolated position, then walk (exact, d is non-decreasing)
+    __device__ __forceinline__ int lower(int l, float v, float hw) const {
+        const int w0 = h->wunion[l][0], w1 = h->wunion[l][1];
+        float f = (v + hw) * h->scale[l];
+        f = fminf(fmaxf(f, 0.f), (float)(w1 - w0));
+        int p = w0 + (int)f;
+        while (p > w0 && d(l, p - 1) >= v) --p;
+        while (p < w1 && d(l, p) < v) ++p;
+        return p;
+    }
+
+    // combined-range index of union position p of layer l: slot order
+    // central, c-1, c+1, c-2, c+2, then position inside the window
+    __device__ __forceinline__ int comb(int l, int p) const {
+        int s = h->sec0[l];
+        const int base = l * S;
+        while ((int)off[base + s + 1] <= p) ++s;
+        const int o = s - h->cen[l];
+        const int k = o == 0 ? 0 : (o < 0 ? -2 * o - 1 : 2 * o);
+        return h->pre[l][k] + (p - h->wfirst[l][k]);
+    }
+};
+
+struct Tracklet {
+    int nh;
+    float chi2, a, b, q;
+    int pos[4];                  // event-local positions, -1 = none
+};
+
+// Collection in layer l (Sec. V-B): the hit nearest `pred` within tol_col,
+// ties to the earliest in combined-range order.  Only hits inside
+// [pred - tol_col - m, pred + tol_col + m] can qualify; the exact float test
+// decides.
+__device__ __forceinline__ int collect(const FindArgs& A, const View& V, int l, float pred, float& dsel) {
+    const float m = 1e-5f * (1.f + fabsf(pred) + A.tol_col);
+    const float lo = pred - A.tol_col - m, hi = pred + A.tol_col + m;
+    const int w1 = V.h->wunion[l][1];
+    int bi = -1, bc = -1;
+    float bd = 0.f;
+    for (int p = V.lower(l, lo, A.hw[l]); p < w1; ++p) {
+        const float dv = V.d(l, p);
+        if (dv > hi) break;
+        const float dist = fabsf(dv - pred);
+        if (!(dist <= A.tol_col)) continue;
+        if (bi < 0 || dist < bd) {
+            bi = p;
+            bd = dist;
+            bc = -1;
+            dsel = dv;
+        } else if (dist == bd) {
+            if (bc < 0) bc = V.comb(l, bi);
+            const int cp = V.comb(l, p);
+            if (cp < bc) {
+                bi = p;
+                bc = cp;
+                dsel = dv;
+            }
+        }
+    }
+    return bi;
+}
+
+// Exact evaluation of the anchor pair (pos_a, pos_b) of direction DIR:
+// pair cuts, collection, fit, chi2 cut (Sec. V-B).
+template <int DIR>
+__device__ __forceinline__ bool eval_pair(const FindArgs& A, const View& V, int pos_a, int pos_b, float da, float db,
+                                          Tracklet& out) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    constexpr int lc0 = DIR ? 2 : 1, lc1 = DIR ? 0 : 3;
+    const float dzab = A.z[lb] - A.z[la];
+    const float dzk = A.z_kink - A.z[la];
+    const float sr = (db - da) / dzab;
+    if (!(fabsf(sr) <= A.slope_tol)) return false;
+    const float dk = da + sr * dzk;
+    if (!(fabsf(dk) <= A.tol_kink)) return false;
+    float dl[4] = {0.f, 0.f, 0.f, 0.f};
+    bool present[4] = {false, false, false, false};
+    out.pos[0] = out.pos[1] = out.pos[2] = out.pos[3] = -1;
+    dl[la] = da;
+    present[la] = true;
+    out.pos[la] = pos_a;
+    dl[lb] = db;
+    present[lb] = true;
+    out.pos[lb] = pos_b;
+    int nh = 2;
+    {
+        const float pred = da + sr * (A.z[lc0] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = collect(A, V, lc0, pred, dsel);
+        if (bi >= 0) {
+            dl[lc0] = dsel;
+            present[lc0] = true;
+            out.pos[lc0] = bi;
+            ++nh;
+        }
+    }
+    {
+        const float pred = da + sr * (A.z[lc1] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = collect(A, V, lc1, pred, dsel);
+        if (bi >= 0) {
+            dl[lc1] = dsel;
+            present[lc1] = true;
+            out.pos[lc1] = bi;
+            ++nh;
+        }
+    }
+    if (nh < 3) return false;
+    float fa, fb, fq, c2;
+    if (!fit32(dl, present, A, fa, fb, fq, c2)) return false;
+    const float c2n = c2 / (float)(nh - 1);
+    if (!(c2n <= A.chi2ndof_max)) return false;
+    out.nh = nh;
+    out.chi2 = c2;
+    out.a = fa;
+    out.b = fb;
+    out.q = fq;
+    return true;
+}
+
+// Band of d_b that can pass the kink cut |da (1 - r) + db r| <= tol_kink,
+// r = (z_kink - z_a)/(z_b - z_a): db within (+-tol_kink)/r - da (1 - r)/r,
+// widened far beyond float rounding (it only bounds the search).
+template <int DIR>
+__device__ __forceinline__ void kink_band(const FindArgs& A, float da, float& blo, float& bhi) {
+    constexpr int lb = DIR ? 1 : 2;
+    const float r = A.band_r[DIR];
+    blo = -INFINITY;
+    bhi = INFINITY;
+    if (fabsf(r) > 1e-3f) {
+        const float mag = (1.f + fabsf(da) + A.hw[lb]) * (1.f + fabsf(r));
+        const float eps = 1e-5f * mag;
+        const float c = da * A.band_k1[DIR];
+        const float w = (A.tol_kink + eps) * A.band_inv_r[DIR];
+        float e0 = -w - c, e1 = w - c;
+        if (e0 > e1) {
+            const float t = e0;
+            e0 = e1;
+            e1 = t;
+        }
+        blo = e0 - 1e-5f * (1.f + fabsf(e0));
+        bhi = e1 + 1e-5f * (1.f + fabsf(e1));
+    }
+}
+
+__device__ __forceinline__ bool better(int nh, float c2, long long key, int o_nh, float o_c2, long long o_key) {
+    return o_nh > nh || (o_nh == nh && (o_c2 < c2 || (o_c2 == c2 && o_key < key)));
+}
+
+// Fast path of one direction: every valid tracklet, in any order; returns
+// their count, or stops as soon as it exceeds n_candidates.
+template <int G, int DIR>
+__device__ __forceinline__ int fast_dir(const FindArgs& A, const View& V, int gl, uint32_t gmask, int& b_nh,
+                                        float& b_c2, int& b_pa, int& b_pb) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const int wa0 = V.h->wunion[la][0], wa1 = V.h->wunion[la][1];
+    const int wb1 = V.h->wunion[lb][1];
+    int lane_valid = 0, l_nh = 0, l_pa = -1, l_pb = -1;
+    float l_c2 = 0.f;
+    long long l_key = LLONG_MAX;
+    int total = 0;
+    for (int base = wa0; base < wa1; base += G) {
+        const int pa = base + gl;
+        if (pa < wa1) {
+            const float da = V.d(la, pa);
+            float blo, bhi;
+            kink_band<DIR>(A, da, blo, bhi);
+            for (int pb = V.lower(lb, blo, A.hw[lb]); pb < wb1; ++pb) {
+                const float db = V.d(lb, pb);
+                if (db > bhi) break;
+                Tracklet tk;
+                if (!eval_pair<DIR>(A, V, pa, pb, da, db, tk)) continue;
+                ++lane_valid;
+                const long long key = ((long long)V.comb(la, pa) << 32) | (long long)(uint32_t)V.comb(lb, pb);
+                if (better(l_nh, l_c2, l_key, tk.nh, tk.chi2, key)) {
+                    l_nh = tk.nh;
+                    l_c2 = tk.chi2;
+                    l_key = key;
+                    l_pa = pa;
+                    l_pb = pb;
+                }
+            }
+        }
+        total = lane_valid;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) total += __shfl_xor_sync(gmask, total, o, G);
+        if (total > A.n_cand) return total;
+    }
+    if (total == 0) return 0;
+    int k_nh = l_nh, k_lane = gl;
+    float k_c2 = l_c2;
+    long long k_key = l_key;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const int o_nh = __shfl_xor_sync(gmask, k_nh, o, G);
+        const float o_c2 = __shfl_xor_sync(gmask, k_c2, o, G);
+        const long long o_key = __shfl_xor_sync(gmask, k_key, o, G);
+        const int o_lane = __shfl_xor_sync(gmask, k_lane, o, G);
+        if (better(k_nh, k_c2, k_key, o_nh, o_c2, o_key)) {
+            k_nh = o_nh;
+            k_c2 = o_c2;
+            k_key = o_key;
+            k_lane = o_lane;
+        }
+    }
+    b_nh = k_nh;
+    b_c2 = k_c2;
+    b_pa = __shfl_sync(gmask, l_pa, k_lane, G);
+    b_pb = __shfl_sync(gmask, l_pb, k_lane, G);
+    return total;
+}
+
+// Union position of combined-range index i of layer l (slot walk).
+__device__ __forceinline__ int slot_pos(const GroupHead* h, int l, int n_sec, int i) {
+    for (int k = 0; k < n_sec; ++k) {
+        const int sz = h->wsize[l][k];
+        if (i < h->pre[l][k] + sz) return h->wfirst[l][k] + (i - h->pre[l][k]);
+    }
+    return -1;
+}
+
+// Ordered path: the valid tracklets whose first anchor is combined index
+// ia, in combined order; returns how many (at most `limit`) and the best of
+// them (strictly better replaces, so the earliest wins ties).
+template <int DIR>
+__device__ __forceinline__ int scan_anchor(const FindArgs& A, const View& V, int ia, int limit, int& best_nh,
+                                           float& best_c2, int& best_pa, int& best_pb) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const int pos_a = slot_pos(V.h, la, A.n_sec, ia);
+    const float da = V.d(la, pos_a);
+    float blo, bhi;
+    kink_band<DIR>(A, da, blo, bhi);
+    const int wb1 = V.h->wunion[lb][1];
+    const int p0 = V.lower(lb, blo, A.hw[lb]);
+    int p1 = p0;
+    while (p1 < wb1 && V.d(lb, p1) <= bhi) ++p1;
+    int nvalid = 0;
+    if (p0 >= p1) return 0;
+    for (int k = 0; k < A.n_sec && nvalid < limit; ++k) {
+        const int f = max(V.h->wfirst[lb][k], p0);
+        const int e = min(V.h->wfirst[lb][k] + V.h->wsize[lb][k], p1);
+        for (int pos_b = f; pos_b < e; ++pos_b) {
+            const float db = V.d(lb, pos_b);
+            Tracklet tk;
+            if (!eval_pair<DIR>(A, V, pos_a, pos_b, da, db, tk)) continue;
+            ++nvalid;
+            if (tk.nh > best_nh || (tk.nh == best_nh && tk.chi2 < best_c2)) {
+                best_nh = tk.nh;
+                best_c2 = tk.chi2;
+                best_pa = pos_a;
+                best_pb = pos_b;
+            }
+            if (nvalid >= limit) break;
+        }
+    }
+    return nvalid;
+}
+
+// Ordered path of one direction (lanes take consecutive first anchors; a
+// prefix count over lanes keeps exactly the first n_candidates).
+template <int G, int DIR>
+__device__ __forceinline__ void ordered_dir(const FindArgs& A, const View& V, int na, int gl, uint32_t gmask,
+                                            int& best_nh, float& best_c2, int& best_pa, int& best_pb) {
+    int count = 0;
+    for (int ia0 = 0; ia0 < na && count < A.n_cand; ia0 += G) {
+        const int ia = ia0 + gl;
+        const int rem = A.n_cand - count;
+        int l_nh = 0, l_pa = -1, l_pb = -1;
+        float l_c2 = 0.f;
+        int nvalid = 0;
+        if (ia < na) nvalid = scan_anchor<DIR>(A, V, ia, rem, l_nh, l_c2, l_pa, l_pb);
+        int incl = nvalid;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const int v = __shfl_up_sync(gmask, incl, o, G);
+            if (gl >= o) incl += v;
+        }
+        const int total = __shfl_sync(gmask, incl, G - 1, G);
+        if (total == 0) continue;
+        const int prefix = incl - nvalid;
+        const int limit = max(0, min(rem - prefix, nvalid));
+        if (limit == 0) {
+            l_nh = 0;
+        } else if (limit < nvalid) {
+            l_nh = 0;
+            l_c2 = 0.f;
+            scan_anchor<DIR>(A, V, ia, limit, l_nh, l_c2, l_pa, l_pb);
+        }
+        int k_nh = l_nh, k_lane = gl;
+        float k_c2 = l_c2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const int o_nh = __shfl_xor_sync(gmask, k_nh, o, G);
+            const float o_c2 = __shfl_xor_sync(gmask, k_c2, o, G);
+            const int o_lane = __shfl_xor_sync(gmask, k_lane, o, G);
+            if (better(k_nh, k_c2, k_lane, o_nh, o_c2, o_lane)) {
+                k_nh = o_nh;
+                k_c2 = o_c2;
+                k_lane = o_lane;
+            }
+        }
+        const int w_pa = __shfl_sync(gmask, l_pa, k_lane, G);
+        const int w_pb = __shfl_sync(gmask, l_pb, k_lane, G);
+        if (k_nh > best_nh || (k_nh == best_nh && k_nh > 0 && k_c2 < best_c2)) {
+            best_nh = k_nh;
+            best_c2 = k_c2;
+            best_pa = w_pa;
+            best_pb = w_pb;
+        }
+        count += min(total, rem);
+    }
+}
+
+template <int G, int DIR>
+__device__ __forceinline__ void search_direction(const FindArgs& A, const View& V, int gl, uint32_t gmask,
+                                                 int& best_nh, float& best_c2, int& best_pa, int& best_pb) {
+    constexpr int la = DIR ? 3 : 0;
+    const int total = fast_dir<G, DIR>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    if (total > A.n_cand) {
+        best_nh = 0;
+        best_c2 = 0.f;
+        best_pa = best_pb = -1;
+        const int na = V.h->wunion[la][1] - V.h->wunion[la][0];
+        ordered_dir<G, DIR>(A, V, na, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    }
+}
+
+// One VELO track t of event e.  X / off: the event's hit x and bank offsets
+// (event-local); hb: global index of the event's first hit.
+template <int G>
+__device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head, const float* X, const uint32_t* off,
+                                              uint32_t hb, int e, uint32_t t, int gl, uint32_t gmask) {
+    const int S = A.S, n_sec = A.n_sec;
+    const float vx = A.vx[t], vy = A.vy[t], vtx = A.vtx[t], vty = A.vty[t];
+    const bool backward = (A.vflags[t] & 1u) != 0;
+
+    // Extrapolation (Sec. V-A): lane l computes layer l.
+    LayerPred mine;
+    mine.hi = mine.lo = 0.f;
+    mine.c = 0;
+    mine.u = 0.0;
+    if (gl < 4) mine = predict(A, vx, vy, vtx, vty, gl);
+    View V;
+    V.h = head;
+    V.X = X;
+    V.off = off;
+    V.S = S;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        V.hi[l] = __shfl_sync(gmask, mine.hi, l, G);
+        V.lo[l] = __shfl_sync(gmask, mine.lo, l, G);
+    }
+    const double u0 = __shfl_sync(gmask, mine.u, 0, G);
+    const double x_max = (double)A.x_min + (double)A.S * (double)A.pitch;
+    const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= x_max);
+
+    if (gl == 0) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
+        A.qop[t] = 0.f;
+        A.chi2[t] = 0.f;
+        A.xo[t] = vx;
+        A.txo[t] = vtx;
+        A.nhits[t] = 0;
+        A.found[t] = 0;
+    }
+    if (!accept) {
+        if (A.win)
+            for (int j = gl; j < 4 * n_sec * 2; j += G) A.win[(size_t)t * 4 * n_sec * 2 + j] = -1;
+        return;
+    }
+
+    // Windows (Sec. V-A): union of the layer's windows, then each slot's part.
+    if (gl < 4) {
+        const int l = gl, c = mine.c;
+        const float hw = A.hw[l];
+        const int s0 = max(c - n_sec / 2, 0), s1 = min(c + (n_sec - 1) / 2, S - 1);
+        const int ra = (int)off[l * S + s0], rb = (int)off[l * S + s1 + 1];
+        int a = ra, b = rb;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (V.d(l, m) >= -hw) b = m; else a = m + 1;
+        }
+        const int w0 = a;
+        b = rb;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (V.d(l, m) > hw) b = m; else a = m + 1;
+        }
+        head->wunion[l][0] = w0;
+        head->wunion[l][1] = a;
+        head->sec0[l] = s0;
+        head->cen[l] = c;
+        head->scale[l] = a > w0 ? (float)(a - w0) / (2.f * hw) : 0.f;
+    }
+    __syncwarp(gmask);
+    for (int j = gl; j < 4 * n_sec; j += G) {
+        const int l = j / n_sec, k = j % n_sec;
+        const int s = head->cen[l] + ((k + 1) >> 1) * ((k & 1) ? -1 : 1);
+        int first = 0, size = 0;
+        if (s >= 0 && s < S) {
+            first = max((int)off[l * S + s], head->wunion[l][0]);
+            size = max(0, min((int)off[l * S + s + 1], head->wunion[l][1]) - first);
+        }
+        head->wfirst[l][k] = first;
+        head->wsize[l][k] = size;
+        if (A.win) {
+            int16_t* wp = A.win + (((size_t)t * 4 + l) * n_sec + k) * 2;
+            int16_t v0 = -1, v1 = -1;
+            if (size > 0) {
+                const long long rel = (long long)first - (long long)off[l * S];
+                if (rel > 32767 || size > 32767) {
+                    report(A.status, UT_ERR_WIN16, e, (long long)(t - A.trk_off[e]));
+                } else {
+                    v0 = (int16_t)rel;
+                    v1 = (int16_t)size;
+                }
+            }
+            wp[0] = v0;
+            wp[1] = v1;
+        }
+    }
+    __syncwarp(gmask);
+    if (gl < 4) {
+        int pre = 0;
+        for (int k = 0; k < n_sec; ++k) {
+            head->pre[gl][k] = pre;
+            pre += head->wsize[gl][k];
+        }
+    }
+    __syncwarp(gmask);
+    int any = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) any |= head->wunion[l][1] - head->wunion[l][0];
+    if (any == 0) return;
+
+    // Tracklet search (Sec. V-B): forward, then backward only if forward
+    // found no valid tracklet.
+    int best_nh = 0, best_dir = 0, best_pa = -1, best_pb = -1;
+    float best_c2 = 0.f;
+    search_direction<G, 0>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    if (best_nh == 0) {
+        best_dir = 1;
+        search_direction<G, 1>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    }
+    if (best_nh == 0 || gl != 0) return;
+
+    // Re-evaluate the selected tracklet for its hits and fit.
+    Tracklet tk;
+    if (best_dir == 0)
+        eval_pair<0>(A, V, best_pa, best_pb, V.d(0, best_pa), V.d(2, best_pb), tk);
+    else
+        eval_pair<1>(A, V, best_pa, best_pb, V.d(3, best_pa), V.d(1, best_pb), tk);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.pos[l] >= 0 ? (int)(hb + tk.pos[l]) : -1;
+    A.qop[t] = tk.q;
+    A.chi2[t] = tk.chi2;
+    A.xo[t] = vx + tk.a;
+    A.txo[t] = vtx + tk.b;
+    A.nhits[t] = (uint8_t)tk.nh;
+    A.found[t] = 1;
+}
+
+// Host: fill FindArgs (derived constants in float, one op per statement;
+// the host compiler runs with -ffp-contract=off).
+int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int n_events,
+                   uint32_t n_tracks, const compass_params* p, compass_tracks* out, int16_t* win, FindArgs& A);
+
+}  // namespace utc
