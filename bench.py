@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
-    ap.add_argument("--form", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--form", default="batched", choices=["batched", "fused", "plain"])
+    ap.add_argument("--autotune", action="store_true", help="pick the batched launch shape by a sweep")
+    ap.add_argument("--x-cap", type=int, default=8192)
     ap.add_argument("--tracks-per-warp", type=int, default=4)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -184,7 +186,11 @@ def algorithmic_bytes(batch):
     find = 4 * H + 4 * (E * B + 1) + 17 * T + 4 * (E + 1) + 34 * T
     sort_b = 2 * 15 * H + 4 * (E * B + 1)
     fit = 17 * T + 16 * T + 16 * T + 4 * 4 * T
-    return {"ut_decode": decode, "compass_find": find, "ut_sort_hits": sort_b, "compass_fit": fit}
+    # one persistent kernel: decode traffic + VELO in + track slots out
+    # (the search reads the event's hits from shared memory)
+    batched = decode + 17 * T + 4 * (E + 1) + 34 * T
+    return {"ut_decode": decode, "compass_find": find, "ut_sort_hits": sort_b, "compass_fit": fit,
+            "ut_run_batched": batched}
 
 
 def main():
@@ -216,15 +222,26 @@ def main():
     tpw, blk = args.tracks_per_warp, args.block
     E = batch.n_events
 
-    kern = ["ut_decode", "ut_sort_hits", "compass_find", "compass_fit"] if args.form == "plain" \
-        else ["ut_decode", "compass_find"]
+    kern = {"plain": ["ut_decode", "ut_sort_hits", "compass_find", "compass_fit"],
+            "fused": ["ut_decode", "compass_find"],
+            "batched": ["ut_run_batched"]}[args.form]
+    cfg = g.LaunchConfig(tpw, blk, args.x_cap, 8192)
+    tune_table = None
+    if args.form == "batched" and args.autotune:
+        from paper_2002_11529_gb300 import autotune
+        cfg, tune_table = autotune.autotune(pipe, reps=3, flush=flush)
+    runner = g.GraphRunner(pipe, cfg) if args.form == "batched" else None
 
     def step(ev=None):
         """One pass; ev: list of (start, end) event pairs per kernel."""
         def mark(i, which):
             if ev is not None:
                 ev[i][which].record(stream)
-        if args.form == "plain":
+        if args.form == "batched":
+            mark(0, 0)
+            runner.replay()
+            mark(0, 1)
+        elif args.form == "plain":
             mark(0, 0)
             g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, False, pipe.workspace, stream)
             mark(0, 1); mark(1, 0)
@@ -348,7 +365,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded generator standing in for the LHCb minbias sample)",
         "config": workload_config(args.workload, batch, args.form,
-                                  {"tracks_per_warp": tpw, "block": blk,
+                                  {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block,
+                                   "x_cap": cfg.x_cap, "graph": args.form == "batched",
+                                   "autotuned": tune_table is not None,
                                    "parallelism": f"events sharded, {world} independent replicas" if world > 1
                                    else "single GPU"}),
         "latency_ms": {"p50": p(0.5), "p99": p(0.99), "what": "one step = one batch"},
@@ -356,6 +375,9 @@ def main():
         "kernels": kinfo,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": nk * args.steps,
+        "autotune": None if tune_table is None else [
+            {"tracks_per_warp": c.tracks_per_warp, "block": c.block, "x_cap": c.x_cap, "ms": round(m, 4)}
+            for c, m in tune_table],
         "clocks": clk,
         "wall_s": wall,
     }

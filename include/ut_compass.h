@@ -225,6 +225,35 @@ int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int 
 int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint32_t n_tracks,
                 const compass_params* p, compass_tracks* inout, void* stream);
 
+/* Launch shape of the batched form (0 in a field = its default). */
+typedef struct ut_launch_config {
+    int tracks_per_warp;    /* 1, 2 or 4 VELO tracks per warp (default 4)      */
+    int block;              /* 128, 256 or 512 threads per block (default 256) */
+    int x_cap;              /* hits of an event kept in shared memory for the
+                               search (default 8192, at most 32768; larger
+                               events are searched from global memory)       */
+    int stage_words;        /* raw words of an event staged by one bulk copy
+                               (multiple of 4, default 8192, at most 32768;
+                               larger events are read from global memory)    */
+} ut_launch_config;
+
+/*
+ * ut_run_batched -- the whole path (Sec. IV decoding with the per-sector
+ * sort, Sec. V window search, tracklet finding and fit) for a batch of
+ * events in ONE persistent kernel launch, suitable for CUDA-graph capture.
+ * Blocks take events from a ticket counter; each decodes an event (as
+ * ut_decode with sorted = 1), keeps its hit x in shared memory and runs
+ * compass_find's search on the event's VELO tracks.
+ * Arguments as ut_decode (raw, ev_off, hits_out, workspace of
+ * ut_decode_workspace_size(n_events) bytes) and compass_find (velo,
+ * n_tracks, params, tracks_out).  Outputs are identical to ut_decode
+ * (sorted) followed by compass_find.  cfg may be NULL (defaults).
+ */
+int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, const uint64_t* d_ev_off,
+                   int n_events, const velo_tracks* velo, uint32_t n_tracks, const compass_params* p,
+                   ut_hits* hits_out, compass_tracks* tracks_out, const ut_launch_config* cfg,
+                   void* d_workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

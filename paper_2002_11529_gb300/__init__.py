@@ -25,7 +25,7 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPA
 
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
-           "ut_decode_noalloc")
+           "ut_decode_noalloc", "ut_run_batched")
 
 
 class UtGeometry(ctypes.Structure):
@@ -54,6 +54,23 @@ class CompassParamsC(ctypes.Structure):
 
 class CompassTracksC(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found")]
+
+
+class LaunchConfigC(ctypes.Structure):
+    _fields_ = [("tracks_per_warp", ctypes.c_int), ("block", ctypes.c_int), ("x_cap", ctypes.c_int),
+                ("stage_words", ctypes.c_int)]
+
+
+@dataclasses.dataclass(frozen=True)
+class LaunchConfig:
+    """Launch shape of the batched form (0 = library default)."""
+    tracks_per_warp: int = 4
+    block: int = 256
+    x_cap: int = 8192
+    stage_words: int = 8192
+
+    def struct(self) -> LaunchConfigC:
+        return LaunchConfigC(self.tracks_per_warp, self.block, self.x_cap, self.stage_words)
 
 
 _lock = threading.Lock()
@@ -85,6 +102,7 @@ def lib():
                 "compass_find": ([P, P, P, I, U32, P, P, P, I, I, P], I),
                 "compass_fit": ([P, P, P, U32, P, P, P], I),
                 "ut_decode_noalloc": ([P, P, U64, P, I, P, I, P, P], I),
+                "ut_run_batched": ([P, P, U64, P, I, P, U32, P, P, P, P, P, SZ, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -303,6 +321,24 @@ def compass_find(ctx, hits: HitBuffers, velo: VeloBuffers, n_events, params, out
                               int(tracks_per_warp), int(block), _stream(stream)), "compass_find")
 
 
+def ut_run_batched(ctx, raw, n_raw_words, ev_off, n_events, velo: VeloBuffers, params,
+                   hits_out: HitBuffers, tracks_out: TrackBuffers, cfg: LaunchConfig | None = None,
+                   workspace=None, stream=None):
+    """The whole path for a batch in one persistent launch (decode, sort,
+    windows, tracklets, fit)."""
+    ws_bytes = decode_workspace_size(n_events)
+    if workspace is None:
+        workspace = torch.empty((ws_bytes + 15) // 16 * 4, dtype=torch.int32, device=raw.device)
+    h, v, p, o = hits_out.struct(), velo.struct(), params_struct(params), tracks_out.struct()
+    c = (cfg or LaunchConfig()).struct()
+    _check(lib().ut_run_batched(ctx.handle, _ptr(raw), int(n_raw_words), _ptr(ev_off), int(n_events),
+                                ctypes.byref(v), velo.n_tracks, ctypes.byref(p), ctypes.byref(h),
+                                ctypes.byref(o), ctypes.byref(c), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)),
+           "ut_run_batched")
+    return workspace
+
+
 def compass_fit(ctx, hits: HitBuffers, velo: VeloBuffers, params, inout: TrackBuffers, stream=None):
     h, v, p, o = hits.struct(), velo.struct(), params_struct(params), inout.struct()
     _check(lib().compass_fit(ctx.handle, ctypes.byref(h), ctypes.byref(v), velo.n_tracks,
@@ -381,9 +417,35 @@ class Pipeline:
         compass_fit(self.ctx, self.hits_b, self.velo, self.params, self.tracks, stream=stream)
         return self.hits_b
 
+    def run_batched(self, cfg: LaunchConfig | None = None, stream=None):
+        ut_run_batched(self.ctx, self.raw, self.n_words, self.ev_off, self.n_events, self.velo,
+                       self.params, self.hits_a, self.tracks, cfg, self.workspace, stream)
+        return self.hits_a
+
     def run_fused(self, stream=None, tracks_per_warp=1, block=256):
         ut_decode(self.ctx, self.raw, self.n_words, self.ev_off, self.n_events, self.hits_a, True,
                   self.workspace, stream)
         compass_find(self.ctx, self.hits_a, self.velo, self.n_events, self.params, self.tracks,
                      tracks_per_warp=tracks_per_warp, block=block, stream=stream)
         return self.hits_a
+
+
+class GraphRunner:
+    """The batched form of a Pipeline captured once in a CUDA graph and
+    replayed (one graph launch per pass over the batch)."""
+
+    def __init__(self, pipe: Pipeline, cfg: LaunchConfig | None = None):
+        self.pipe = pipe
+        self.cfg = cfg
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            pipe.run_batched(cfg)          # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            pipe.run_batched(cfg)
+
+    def replay(self):
+        self.graph.replay()

@@ -1,0 +1,184 @@
+// Persistent batched decode + Compass: the whole batch in one launch.
+//
+// Each block loops over events taken from a global ticket counter (so
+// events of very different sizes balance across the GPU).  For each event
+// it runs the per-event decode (Sec. IV) -- bulk copy of the raw event into
+// shared memory, hit counting, scan, look-back for the global hit base,
+// sorted SoA written to global memory -- and keeps the decoded x of the
+// event in shared memory, then its lane groups run Compass (Sec. V) on the
+// event's VELO tracks straight from that copy.  Events are independent, so
+// no grid-wide barrier is needed; the look-back only waits for aggregates
+// that earlier tickets publish as soon as they have counted their hits.
+
+#include "compass_track.cuh"
+#include "decode_event.cuh"
+
+namespace utc {
+
+struct BatchedLayout {
+    size_t off_bytes, stage_byte0, sx_byte0, heads_byte0, total;
+};
+
+__host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_words, uint32_t x_cap, int gpb) {
+    BatchedLayout L;
+    L.off_bytes = (size_t)kBigWarps * kKeyBins * 4;
+    L.stage_byte0 = L.off_bytes + (((size_t)(B + 1) * 4 + 15) & ~(size_t)15);
+    L.sx_byte0 = L.stage_byte0 + (size_t)stage_words * 4 + 16;
+    L.heads_byte0 = L.sx_byte0 + (((size_t)x_cap * 4 + 15) & ~(size_t)15);
+    L.total = L.heads_byte0 + (size_t)gpb * sizeof(GroupHead);
+    return L;
+}
+
+template <int G, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeArgs D, const FindArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ int s_event;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t warp_tot[kMaxDecodeThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int B = 4 * D.S;
+    constexpr int gpb = NT / G;
+    const int g = tid / G;
+    const int gl = tid % G;
+    const int lane = tid & 31;
+    const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, gpb);
+    DecodeSmem sm;
+    sm.bigcnt = reinterpret_cast<uint32_t*>(smem);
+    sm.off = reinterpret_cast<uint32_t*>(smem + L.off_bytes);
+    size_t sb = L.stage_byte0;
+    sb += (16u - ((smem_u32(smem) + (uint32_t)sb) & 15u)) & 15u;
+    sm.stage = reinterpret_cast<uint32_t*>(smem + sb);
+    sm.mbar = &mbar;
+    sm.s_base = &s_base;
+    sm.warp_tot = warp_tot;
+    float* sx = reinterpret_cast<float*>(smem + L.sx_byte0);
+    GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.heads_byte0);
+
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    uint32_t phase = 0;
+    bool tma_ok = true;
+    for (;;) {
+        __syncthreads();  // previous event's readers are done with shared memory
+        if (tid == 0) s_event = (int)atomicAdd(D.ticket, 1u);
+        __syncthreads();
+        const int e = s_event;
+        if (e >= D.n_events) break;
+        decode_event<true>(D, e, sm, phase, tma_ok, sx, A.x_cap);
+        __syncthreads();
+        const uint32_t total = sm.off[B];
+        const unsigned long long base = s_base;
+        if (base + total > (unsigned long long)D.capacity) continue;  // reported by decode_event
+        const float* X = total <= A.x_cap ? sx : D.x + base;
+        const uint32_t t0 = A.trk_off[e], t1 = A.trk_off[e + 1];
+        for (uint32_t t = t0 + g; t < t1; t += gpb)
+            compass_track<G>(A, heads + g, X, sm.off, (uint32_t)base, e, t, gl, gmask);
+    }
+    drain_stage(sm, phase, tma_ok);
+}
+
+template <int G, int NT>
+static int launch_batched(const DecodeArgs& D, const FindArgs& A, int num_sms, cudaStream_t st) {
+    const int B = 4 * D.S;
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, NT / G);
+    const size_t smem = L.total;
+    auto kern = ut_batched_kernel<G, NT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return UT_ERR_CUDA;
+    // occupancy of this instance, queried once per device and shared-memory
+    // size (so that a later call inside a stream capture makes no query)
+    static int cached_dev[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    static size_t cached_smem[16];
+    static int cached_per_sm[16];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return UT_ERR_CUDA;
+    const int slot = dev & 15;
+    int per_sm = 0;
+    if (cached_dev[slot] == dev && cached_smem[slot] == smem) {
+        per_sm = cached_per_sm[slot];
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1)
+            return UT_ERR_CUDA;
+        cached_per_sm[slot] = per_sm;
+        cached_smem[slot] = smem;
+        cached_dev[slot] = dev;
+    }
+    const long long want = (long long)num_sms * per_sm;
+    const int grid = (int)(want < D.n_events ? want : D.n_events);
+    kern<<<grid, NT, smem, st>>>(D, A);
+    return check_cuda(cudaGetLastError());
+}
+
+template <int G>
+static int launch_batched_g(const DecodeArgs& D, const FindArgs& A, int block, int num_sms, cudaStream_t st) {
+    switch (block) {
+        case 128: return launch_batched<G, 128>(D, A, num_sms, st);
+        case 256: return launch_batched<G, 256>(D, A, num_sms, st);
+        case 512: return launch_batched<G, 512>(D, A, num_sms, st);
+        default: return UT_ERR_ARG;
+    }
+}
+
+}  // namespace utc
+
+using namespace utc;
+
+extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, const uint64_t* d_ev_off,
+                              int n_events, const velo_tracks* velo, uint32_t n_tracks, const compass_params* p,
+                              ut_hits* hits_out, compass_tracks* tracks_out, const ut_launch_config* cfg,
+                              void* d_workspace, size_t workspace_bytes, void* stream) {
+    if (!ctx || !hits_out || !hits_out->hit_off || !velo || !p || !tracks_out || n_events < 0) return UT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_events == 0) return check_cuda(cudaMemsetAsync(hits_out->hit_off, 0, sizeof(uint32_t), st));
+    if (!d_raw || !d_ev_off || !d_workspace) return UT_ERR_ARG;
+    if (!hits_out->x || !hits_out->z || !hits_out->sector || !hits_out->layer || !hits_out->id) return UT_ERR_ARG;
+    if (((uintptr_t)d_raw & 15u) != 0 || ((uintptr_t)d_workspace & 15u) != 0) return UT_ERR_ARG;
+    if (workspace_bytes < ut_decode_workspace_size(n_events)) return UT_ERR_ARG;
+    int tpw = cfg ? cfg->tracks_per_warp : 0, block = cfg ? cfg->block : 0;
+    int x_cap = cfg ? cfg->x_cap : 0, stage_words = cfg ? cfg->stage_words : 0;
+    if (tpw == 0) tpw = 4;
+    if (block == 0) block = 256;
+    if (x_cap == 0) x_cap = 8192;
+    if (stage_words == 0) stage_words = 8192;
+    if (x_cap < 0 || x_cap > 32768 || stage_words < 0 || stage_words > 32768 || (stage_words & 3) != 0)
+        return UT_ERR_ARG;
+    FindArgs A;
+    int rc = make_find_args(ctx, hits_out, velo, n_events, n_tracks, p, tracks_out, nullptr, A);
+    if (rc != UT_OK) return rc;
+    A.x_cap = (uint32_t)x_cap;
+    const int S = ctx->geom.n_sectors;
+    DecodeArgs D;
+    D.raw = d_raw;
+    D.n_words = n_raw_words;
+    D.ev_off = d_ev_off;
+    D.n_events = n_events;
+    D.S = S;
+    D.x = hits_out->x;
+    D.z = hits_out->z;
+    D.sector = hits_out->sector;
+    D.layer = hits_out->layer;
+    D.id = hits_out->id;
+    D.hit_off = hits_out->hit_off;
+    D.capacity = hits_out->capacity;
+    D.x_min = ctx->geom.x_min;
+    D.sector_pitch = ctx->geom.sector_pitch;
+    D.half_pitch = ctx->geom.strip_pitch * 0.5f;
+    D.strips = ctx->geom.strips;
+    for (int l = 0; l < 4; ++l) D.zl[l] = ctx->geom.z[l];
+    D.ticket = static_cast<unsigned int*>(d_workspace);
+    D.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
+    D.status = ctx->d_status;
+    D.stage_words = (uint32_t)stage_words;
+    if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
+    switch (tpw) {
+        case 1: return launch_batched_g<32>(D, A, block, ctx->num_sms, st);
+        case 2: return launch_batched_g<16>(D, A, block, ctx->num_sms, st);
+        case 4: return launch_batched_g<8>(D, A, block, ctx->num_sms, st);
+        default: return UT_ERR_ARG;
+    }
+}

@@ -15,164 +15,32 @@
 #include <mutex>
 #include <unordered_map>
 
-#include "common.cuh"
+#include "decode_event.cuh"
 
 namespace utc {
 
 constexpr int kDecodeThreads = 256;
-constexpr int kSmallBank = 64;          // banks up to this size rank by direct counting
-constexpr int kBigWarps = 2;            // warps that sort larger banks
-constexpr int kKeyBins = 1024;          // half-strip keys (strips <= 512)
-constexpr uint32_t kStageWordsDefault = 8192;
-
-// Tile (event) state of the look-back, 64-bit: flag in bits 62-63.
-constexpr unsigned long long kFlagAggregate = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-
-struct DecodeArgs {
-    const uint32_t* raw;
-    uint64_t n_words;
-    const uint64_t* ev_off;
-    int n_events;
-    int S;
-    float* x;
-    float* z;
-    uint16_t* sector;
-    uint8_t* layer;
-    uint32_t* id;
-    uint32_t* hit_off;
-    uint32_t capacity;
-    float x_min, sector_pitch, half_pitch;
-    int strips;
-    float zl[4];
-    unsigned int* ticket;
-    unsigned long long* tile_state;
-    unsigned long long* status;
-    uint32_t stage_words;
-};
-
-struct HitOut {
-    float* x;
-    float* z;
-    uint16_t* sector;
-    uint8_t* layer;
-    uint32_t* id;
-};
-
-// Decoded hit parameters of word w in sector s of layer l (Sec. IV):
-// x = x0_s + (h + 1/2) * pitch/2 with x0_s = s * sector_pitch + x_min.
-// Each float operation is a separate IEEE op (no contraction: -fmad=false).
-__device__ __forceinline__ void write_hit(const DecodeArgs& a, uint32_t o, int l, int s, uint32_t w) {
-    const uint32_t h = half_strip(w);
-    const float x0 = __fadd_rn(__fmul_rn((float)s, a.sector_pitch), a.x_min);
-    const float c = __fmul_rn(__fadd_rn((float)h, 0.5f), a.half_pitch);
-    a.x[o] = __fadd_rn(x0, c);
-    a.z[o] = a.zl[l];
-    a.sector[o] = (uint16_t)s;
-    a.layer[o] = (uint8_t)l;
-    a.id[o] = ((uint32_t)l << 24) | ((uint32_t)s << 16) | w;
-}
-
-// Block-wide exclusive scan of cnt[0..n) in place; returns the total.
-// n may exceed the block size (each thread scans a contiguous run).
-__device__ uint32_t block_exclusive_scan(uint32_t* cnt, int n, uint32_t* warp_tot) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int per = (n + nt - 1) / nt;
-    const int b0 = min(tid * per, n), b1 = min(b0 + per, n);
-    uint32_t local = 0;
-    for (int b = b0; b < b1; ++b) local += cnt[b];
-    // warp inclusive scan of the per-thread sums
-    const int lane = tid & 31, wid = tid >> 5;
-    uint32_t v = local;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += t;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = nt >> 5;
-        uint32_t w = lane < nw ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += t;
-        }
-        if (lane < nw) warp_tot[lane] = w;  // inclusive per warp
-    }
-    __syncthreads();
-    uint32_t run = (v - local) + (wid > 0 ? warp_tot[wid - 1] : 0u);
-    const uint32_t total = warp_tot[(nt >> 5) - 1];
-    for (int b = b0; b < b1; ++b) {
-        const uint32_t c = cnt[b];
-        cnt[b] = run;
-        run += c;
-    }
-    __syncthreads();
-    return total;
-}
-
-// Decoupled look-back (single-pass prefix sum across events): returns the
-// sum of the aggregates of all events before `e`.  Executed by one warp.
-__device__ unsigned long long lookback(unsigned long long* tile_state, int e, unsigned long long* status) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long excl = 0;
-    int j = e - 1;
-    long long spins = 0;
-    while (j >= 0) {
-        const int idx = j - lane;
-        unsigned long long s = idx >= 0 ? ld_volatile_u64(tile_state + idx) : kFlagPrefix;
-        // wait until every lane sees a published state
-        while (__any_sync(0xffffffffu, (s >> 62) == 0)) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) report(status, UT_ERR_TIMEOUT, e, -1);
-                return excl;
-            }
-            __nanosleep(32);
-            if ((s >> 62) == 0) s = ld_volatile_u64(tile_state + idx);
-        }
-        const uint32_t pmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-        const int stop = pmask ? __ffs(pmask) - 1 : 31;   // lanes 0..stop contribute
-        unsigned long long v = lane <= stop ? (s & kValueMask) : 0ull;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-        excl += v;
-        if (pmask) break;
-        j -= 32;
-    }
-    return excl;
-}
-
-// Stable rank of key[k] among key[0..n) (small banks): number of keys that
-// are smaller, or equal and earlier.
-__device__ __forceinline__ uint32_t rank_small(const uint16_t* w16, uint32_t n, uint32_t k, uint32_t hk) {
-    uint32_t r = 0;
-    for (uint32_t j = 0; j < n; ++j) {
-        const uint32_t hj = min(half_strip(w16[j]), (uint32_t)(kKeyBins - 1));
-        r += (hj < hk) || (hj == hk && j < k);
-    }
-    return r;
-}
-
 template <bool SORT>
 __global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ int s_event;
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t warp_tot[kDecodeThreads / 32];
+    __shared__ uint32_t warp_tot[kMaxDecodeThreads / 32];
 
     const int tid = threadIdx.x;
-    const int S = a.S, B = 4 * S;
-    uint32_t* bigcnt = reinterpret_cast<uint32_t*>(smem);                 // kBigWarps * kKeyBins
-    uint32_t* off = bigcnt + (SORT ? kBigWarps * kKeyBins : 0);          // B + 1
+    const int B = 4 * a.S;
+    DecodeSmem sm;
+    sm.bigcnt = reinterpret_cast<uint32_t*>(smem);                          // kBigWarps * kKeyBins
+    sm.off = sm.bigcnt + (SORT ? kBigWarps * kKeyBins : 0);                 // B + 1
     // stage: first 16-byte aligned shared address after the offsets (the
     // allocation carries 16 bytes of slack for this rounding)
     size_t stage_byte0 = (size_t)((SORT ? kBigWarps * kKeyBins : 0) + B + 1) * 4;
     stage_byte0 += (16u - ((smem_u32(smem) + (uint32_t)stage_byte0) & 15u)) & 15u;
-    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + stage_byte0);
+    sm.stage = reinterpret_cast<uint32_t*>(smem + stage_byte0);
+    sm.mbar = &mbar;
+    sm.s_base = &s_base;
+    sm.warp_tot = warp_tot;
 
     if (tid == 0) {
         s_event = (int)atomicAdd(a.ticket, 1u);
@@ -182,158 +50,10 @@ __global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeA
     __syncthreads();
     const int e = s_event;
     if (e >= a.n_events) return;
-
-    const uint64_t ws = a.ev_off[e], we = a.ev_off[e + 1];
-    const bool ev_ok = we >= ws && we <= a.n_words && (we - ws) >= (uint64_t)B;
-    const uint64_t nw = ev_ok ? we - ws : 0;
-    const uint32_t* evw = a.raw + (ev_ok ? ws : 0);
-
-    // Stage the whole event (16-byte aligned superset) with one bulk copy.
-    if (ev_ok) {
-        const uint64_t al0 = ws & ~3ull, al1 = (we + 3) & ~3ull;
-        const uint64_t words = al1 - al0;
-        if (words <= a.stage_words) {
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&mbar, (uint32_t)(words * 4));
-                const uint32_t* src = a.raw + al0;
-                uint64_t done = 0;
-                while (done < words) {
-                    const uint32_t chunk = (uint32_t)((words - done) < 8192ull ? (words - done) : 8192ull);  // 32 KB
-                    bulk_copy_g2s(stage + done, src + done, chunk * 4, &mbar);
-                    done += chunk;
-                }
-            }
-            if (!mbar_wait_bounded(&mbar, 0)) {
-                if (tid == 0) report(a.status, UT_ERR_TIMEOUT, e, -1);
-            } else {
-                evw = stage + (ws - al0);
-            }
-        }
-    } else if (tid == 0) {
-        report(a.status, UT_ERR_DIR, e, 0);
-    }
-
-    // Hit counting with directory / header checks (one thread per bank).
-    for (int b = tid; b < B; b += kDecodeThreads) {
-        uint32_t n = 0;
-        if (ev_ok) {
-            const uint32_t d = evw[b];
-            if ((uint64_t)d >= (uint64_t)B && (uint64_t)d + 1 <= nw) {
-                const uint32_t hdr = evw[d];
-                const uint32_t nn = hdr & 0xFFFFu;
-                if ((uint64_t)d + 1 + (nn + 1) / 2 > nw) {
-                    report(a.status, UT_ERR_DIR, e, b);
-                } else if ((hdr >> 16) != (uint32_t)b) {
-                    report(a.status, UT_ERR_HEADER, e, b);
-                } else {
-                    n = nn;
-                }
-            } else {
-                report(a.status, UT_ERR_DIR, e, b);
-            }
-        }
-        off[b] = n;
-    }
-    __syncthreads();
-    const uint32_t total = block_exclusive_scan(off, B, warp_tot);
-    if (tid == 0) off[B] = total;
-
-    // Global base of this event: publish the aggregate, look back, publish
-    // the inclusive prefix.
-    if (tid < 32) {
-        if (tid == 0) {
-            st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
-        }
-        unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
-        if (tid == 0) {
-            if (e > 0) st_volatile_u64(a.tile_state + e, kFlagPrefix | ((excl + total) & kValueMask));
-            s_base = excl;
-        }
-    }
-    __syncthreads();
-    const unsigned long long base = s_base;
-    const unsigned long long end = base + total;
-    const bool fits = end <= (unsigned long long)a.capacity;
-    if (!fits && tid == 0) report(a.status, UT_ERR_CAPACITY, -1, -1);
-
-    uint32_t* hit_off = a.hit_off + (size_t)e * B;
-    for (int b = tid; b < B; b += kDecodeThreads) hit_off[b] = (uint32_t)(base + off[b]);
-    if (e == a.n_events - 1 && tid == 0) a.hit_off[(size_t)a.n_events * B] = (uint32_t)end;
-    if (!ev_ok) return;
-
-    // Decode: one thread per hit of the event (bank found by binary search).
-    for (uint32_t i = tid; i < total; i += kDecodeThreads) {
-        const int b = find_bank(off, B, i);
-        const uint32_t k = i - off[b];
-        const uint32_t n = off[b + 1] - off[b];
-        const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
-        const uint32_t w = w16[k];
-        if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
-        uint32_t r = k;
-        if (SORT) {
-            if (n > (uint32_t)kSmallBank) continue;  // ranked below
-            const uint32_t hk = min(half_strip(w), (uint32_t)(kKeyBins - 1));
-            r = rank_small(w16, n, k, hk);
-        }
-        if (fits) write_hit(a, (uint32_t)(base + off[b] + r), b / S, b % S, w);
-    }
-
-    if (SORT) {
-        // Larger banks: counting sort on the half-strip key by one warp per
-        // bank (histogram, exclusive scan of the bins, then a stable pass in
-        // word order where equal keys inside a 32-word chunk are ranked with
-        // a match mask).
-        const int wid = tid >> 5, lane = tid & 31;
-        if (wid < kBigWarps) {
-            uint32_t* cnt = bigcnt + wid * kKeyBins;
-            for (int b0 = wid * 32; b0 < B; b0 += kBigWarps * 32) {
-                const int bl = b0 + lane;
-                const bool big = bl < B && (off[bl + 1] - off[bl]) > (uint32_t)kSmallBank;
-                uint32_t mask = __ballot_sync(0xffffffffu, big);
-                while (mask) {
-                    const int b = b0 + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const uint32_t n = off[b + 1] - off[b];
-                    const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
-                    for (int q = lane; q < kKeyBins; q += 32) cnt[q] = 0;
-                    __syncwarp();
-                    for (uint32_t k = lane; k < n; k += 32)
-                        atomicAdd(&cnt[min(half_strip(w16[k]), (uint32_t)(kKeyBins - 1))], 1u);
-                    __syncwarp();
-                    uint32_t run = 0;
-                    for (int q = 0; q < kKeyBins / 32; ++q) run += cnt[lane * (kKeyBins / 32) + q];
-                    uint32_t incl = run;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
-                        if (lane >= d) incl += t;
-                    }
-                    uint32_t acc = incl - run;
-                    for (int q = 0; q < kKeyBins / 32; ++q) {
-                        const uint32_t c = cnt[lane * (kKeyBins / 32) + q];
-                        cnt[lane * (kKeyBins / 32) + q] = acc;
-                        acc += c;
-                    }
-                    __syncwarp();
-                    for (uint32_t k0 = 0; k0 < n; k0 += 32) {
-                        const uint32_t k = k0 + lane;
-                        const bool valid = k < n;
-                        const uint32_t w = valid ? w16[k] : 0u;
-                        const uint32_t hk = valid ? min(half_strip(w), (uint32_t)(kKeyBins - 1)) : kKeyBins + lane;
-                        const uint32_t peers = __match_any_sync(0xffffffffu, hk);
-                        const uint32_t before = __popc(peers & lanemask_lt());
-                        const uint32_t pos = valid ? cnt[hk] + before : 0u;
-                        __syncwarp();
-                        if (valid && before == 0) cnt[hk] += __popc(peers);
-                        __syncwarp();
-                        if (valid && fits) write_hit(a, (uint32_t)(base + off[b] + pos), b / S, b % S, w);
-                    }
-                    __syncwarp();
-                }
-            }
-        }
-    }
+    uint32_t phase = 0;
+    bool tma_ok = true;
+    decode_event<SORT>(a, e, sm, phase, tma_ok, nullptr, 0);
+    drain_stage(sm, phase, tma_ok);
 }
 
 // ---------------------------------------------------------------------------
