@@ -208,7 +208,7 @@ int ut_sort_hits(ut_ctx* ctx, const ut_hits* in, ut_hits* out, uint32_t* d_perm,
  * d_win (nullable): int16 [n_tracks][4][n_sectors][2] windows as (first hit
  * relative to the event's layer start, size), (-1, -1) when empty;
  * UT_ERR_WIN16 is recorded if a value does not fit.
- * Launch shape: `tracks_per_warp` in {1, 2, 4} (0 = default 1) and
+ * Launch shape: `tracks_per_warp` in {1, 2, 4, 8} (0 = default 1) and
  * `block` threads in {64..1024, multiple of 32} (0 = default 256).
  */
 int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int n_events,
@@ -227,7 +227,7 @@ int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint3
 
 /* Launch shape of the batched form (0 in a field = its default). */
 typedef struct ut_launch_config {
-    int tracks_per_warp;    /* 1, 2 or 4 VELO tracks per warp (default 4)      */
+    int tracks_per_warp;    /* 1, 2, 4 or 8 VELO tracks per warp (default 4)   */
     int block;              /* 128, 256 or 512 threads per block (default 256) */
     int x_cap;              /* hits of an event kept in shared memory for the
                                search (default 8192, at most 32768; larger

@@ -179,6 +179,7 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
         case 1: return launch_batched_g<32>(D, A, block, ctx->num_sms, st);
         case 2: return launch_batched_g<16>(D, A, block, ctx->num_sms, st);
         case 4: return launch_batched_g<8>(D, A, block, ctx->num_sms, st);
+        case 8: return launch_batched_g<4>(D, A, block, ctx->num_sms, st);
         default: return UT_ERR_ARG;
     }
 }

@@ -144,6 +144,48 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
     }
     A.x_cap = 0;
     A.split = 1;
+    // fit factors per presence mask (float, operations in the fit's order)
+    for (int l = 0; l < 4; ++l) {
+        A.wt[l] = A.w * A.t[l];
+        A.wf[l] = A.w * A.f[l];
+    }
+    for (int m = 0; m < 16; ++m) {
+        float S0 = 0.f, St = 0.f, Sf = 0.f, Stt = 0.f, Stf = 0.f, Sff = 0.f;
+        for (int l = 0; l < 4; ++l) {
+            if (!(m & (1 << l))) continue;
+            const float wt = A.wt[l];
+            const float wf = A.wf[l];
+            S0 = S0 + A.w;
+            St = St + wt;
+            Sf = Sf + wf;
+            const float stt = wt * A.t[l];
+            Stt = Stt + stt;
+            const float stf = wt * A.f[l];
+            Stf = Stf + stf;
+            const float sff = wf * A.f[l];
+            Sff = Sff + sff;
+        }
+        const float N11 = S0 + A.px, N12 = St, N13 = Sf, N22 = Stt + A.ptx, N23 = Stf, N33 = Sff;
+        const float D1 = N11;
+        const float L21 = N12 / D1;
+        const float L31 = N13 / D1;
+        const float l21n12 = L21 * N12;
+        const float D2 = N22 - l21n12;
+        const float l31n12 = L31 * N12;
+        const float E32 = N23 - l31n12;
+        const float L32 = E32 / D2;
+        const float l31n13 = L31 * N13;
+        const float l32e32 = L32 * E32;
+        const float D3a = N33 - l31n13;
+        const float D3 = D3a - l32e32;
+        A.fac[m][0] = D1;
+        A.fac[m][1] = D2;
+        A.fac[m][2] = D3;
+        A.fac[m][3] = L21;
+        A.fac[m][4] = L31;
+        A.fac[m][5] = L32;
+        A.fac_ok[m] = (D1 > 0.f) && (D2 > 0.f) && (D3 > 0.f);
+    }
     return UT_OK;
 }
 
@@ -188,6 +230,7 @@ extern "C" int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
         case 1: return launch_find<32>(A, block, ctx->num_sms, st);
         case 2: return launch_find<16>(A, block, ctx->num_sms, st);
         case 4: return launch_find<8>(A, block, ctx->num_sms, st);
+        case 8: return launch_find<4>(A, block, ctx->num_sms, st);
         default: return UT_ERR_ARG;
     }
 }

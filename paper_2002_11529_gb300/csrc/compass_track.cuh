@@ -63,6 +63,14 @@ struct FindArgs {
     float band_r[2], band_inv_r[2], band_k1[2];  // kink-band constants per direction
     uint32_t x_cap;              // hits of an event staged in shared memory
     int split;                   // blocks sharing one event's tracks
+    // The normal matrix of the fit depends only on which layers carry a
+    // hit: its LDL^T factors per presence mask (bit l = layer l), computed
+    // on the host with the same float operations as a per-candidate
+    // factorisation would use.  fac[m] = {D1, D2, D3, L21, L31, L32}; ok[m]
+    // = all pivots positive.  wt, wf: w*t_l and w*f_l.
+    float fac[16][6];
+    int fac_ok[16];
+    float wt[4], wf[4];
 };
 
 // Track prediction in the measured coordinate of layer l:
@@ -88,36 +96,30 @@ __device__ __forceinline__ LayerPred predict(const FindArgs& a, float vx, float 
 }
 
 // Closed-form p-kick fit in float (Sec. III-C): residual model
-// d_l = a + b t_l + q f_l with a Gaussian prior on (a, b); LDL^T solve.
+// d_l = a + b t_l + q f_l with a Gaussian prior on (a, b).  The normal
+// matrix N = sum_l w g_l g_l^T + diag(px, ptx, 0) is accumulated over the
+// present layers in layer order and factorised as LDL^T:
+//   D1 = N11, L21 = N12/D1, L31 = N13/D1, D2 = N22 - L21 N12,
+//   E32 = N23 - L31 N12, L32 = E32/D2, D3 = N33 - L31 N13 - L32 E32;
+// those factors depend only on the presence mask and come from a table
+// (fit_factors, computed with exactly these operations).  Per candidate:
+// right-hand side, forward / diagonal / back substitution, chi2.
 __device__ __forceinline__ bool fit32(const float* d, const bool* present, const FindArgs& A, float& a_o,
                                       float& b_o, float& q_o, float& chi2_o) {
     const float w = A.w;
-    float S0 = 0.f, St = 0.f, Sf = 0.f, Stt = 0.f, Stf = 0.f, Sff = 0.f;
+    int mask = 0;
     float Bd = 0.f, Btd = 0.f, Bfd = 0.f;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         if (!present[l]) continue;
-        const float wt = w * A.t[l];
-        const float wf = w * A.f[l];
-        S0 = S0 + w;
-        St = St + wt;
-        Sf = Sf + wf;
-        Stt = Stt + wt * A.t[l];
-        Stf = Stf + wt * A.f[l];
-        Sff = Sff + wf * A.f[l];
+        mask |= 1 << l;
         Bd = Bd + w * d[l];
-        Btd = Btd + wt * d[l];
-        Bfd = Bfd + wf * d[l];
+        Btd = Btd + A.wt[l] * d[l];
+        Bfd = Bfd + A.wf[l] * d[l];
     }
-    const float N11 = S0 + A.px, N12 = St, N13 = Sf, N22 = Stt + A.ptx, N23 = Stf, N33 = Sff;
-    const float D1 = N11;
-    const float L21 = N12 / D1;
-    const float L31 = N13 / D1;
-    const float D2 = N22 - L21 * N12;
-    const float E32 = N23 - L31 * N12;
-    const float L32 = E32 / D2;
-    const float D3 = N33 - L31 * N13 - L32 * E32;
-    if (!(D1 > 0.f) || !(D2 > 0.f) || !(D3 > 0.f)) return false;
+    if (!A.fac_ok[mask]) return false;
+    const float D1 = A.fac[mask][0], D2 = A.fac[mask][1], D3 = A.fac[mask][2];
+    const float L21 = A.fac[mask][3], L31 = A.fac[mask][4], L32 = A.fac[mask][5];
     const float y1 = Bd;
     const float y2 = Btd - L21 * y1;
     const float y3 = Bfd - L31 * y1 - L32 * y2;
@@ -534,21 +536,23 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
     }
 
     // Windows (Sec. V-A): union of the layer's windows, then each slot's part.
+    // (lane l uses its own prediction: no runtime index into V.hi / V.lo,
+    // which would move them to local memory)
     if (gl < 4) {
         const int l = gl, c = mine.c;
-        const float hw = A.hw[l];
+        const float hw = A.hw[l], uh = mine.hi, ul = mine.lo;
         const int s0 = max(c - n_sec / 2, 0), s1 = min(c + (n_sec - 1) / 2, S - 1);
         const int ra = (int)off[l * S + s0], rb = (int)off[l * S + s1 + 1];
         int a = ra, b = rb;
         while (a < b) {
             const int m = (a + b) >> 1;
-            if (V.d(l, m) >= -hw) b = m; else a = m + 1;
+            if ((X[m] - uh) - ul >= -hw) b = m; else a = m + 1;
         }
         const int w0 = a;
         b = rb;
         while (a < b) {
             const int m = (a + b) >> 1;
-            if (V.d(l, m) > hw) b = m; else a = m + 1;
+            if ((X[m] - uh) - ul > hw) b = m; else a = m + 1;
         }
         head->wunion[l][0] = w0;
         head->wunion[l][1] = a;

@@ -242,7 +242,7 @@ def test_compass_find_matches_oracle(g, name):
     assert_tracks_equal(gpu, orc, b)
 
 
-@pytest.mark.parametrize("tpw,block", [(1, 128), (2, 256), (4, 256), (4, 64)])
+@pytest.mark.parametrize("tpw,block", [(1, 128), (2, 256), (4, 256), (4, 64), (8, 256), (8, 128)])
 def test_compass_launch_shapes(g, tpw, block):
     b = BATCHES["plain64"]()
     gpu = run_compass(g, b, P, tracks_per_warp=tpw, block=block)
