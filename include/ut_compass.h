@@ -254,6 +254,50 @@ int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, con
                    ut_hits* hits_out, compass_tracks* tracks_out, const ut_launch_config* cfg,
                    void* d_workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Alignment (the p-kick fit of Sec. III-C with the selected hits held
+ * fixed, in a detector whose sector g = l*S + s sits at z_l + dz_g, is
+ * shifted by dx_g and has its strips rotated in the plane by gamma_g).
+ * For hit h of track t (state theta_t = (x, tx, qop) at z_velo, VELO state
+ * x_v, y_v, tx_v, ty_v):
+ *   z = z_l + dz_g, y = y_v + ty_v (z - z_velo), T = tan(a_l + gamma_g),
+ *   r = u_h + dx_g + y T - [x + tx (z - z_velo) + k qop (z - z_kink)],
+ *   chi2 = sum_t [ sum_h w r^2 + px (x - x_v)^2 + ptx (tx - tx_v)^2 ],
+ * with w = 1/sigma_hit^2, px = 1/sigma_x_prior^2, ptx = 1/sigma_tx_prior^2,
+ * k = kick_k, z_kink from the compass_params.
+ *   d_track_hits: int32 [n_tracks][4] hit index per layer (-1 = none);
+ *   velo: x, y, tx, ty of the tracks (trk_off, flags unused);
+ *   d_align: float [4S][3] (dx, dz, gamma); d_theta: float [n_tracks][3].
+ * Residuals are formed in double.  Per-sector sums are accumulated in 64-bit
+ * fixed point, so chi2, gradient and blocks are bit-reproducible.
+ */
+size_t ut_align_workspace_size(int n_sectors);
+
+/* chi2 (double, *d_chi2) and its adjoint: d_grad_theta [n_tracks][3]
+ * (d chi2 / d theta), d_grad_align [4S][3] (d chi2 / d align), d_hess_align
+ * [4S][6] the per-sector Gauss-Newton block sum_h 2 w (dr/da)(dr/da)^T
+ * as (xx, xz, xg, zz, zg, gg); each nullable.  Sectors without hits get
+ * exactly zero.  Workspace: ut_align_workspace_size(S) bytes. */
+int ut_align_chi2(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* d_track_hits,
+                  uint32_t n_tracks, const compass_params* p, const float* d_align, const float* d_theta,
+                  double* d_chi2, float* d_grad_theta, float* d_grad_align, float* d_hess_align,
+                  void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Per-track refit: theta minimising each track's chi2 for the given
+ * alignment (closed form, double); tracks with fewer than 3 hits get the
+ * VELO state with qop = 0. */
+int ut_align_refit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* d_track_hits,
+                   uint32_t n_tracks, const compass_params* p, const float* d_align, float* d_theta,
+                   void* stream);
+
+/* Reduced Gauss-Newton Hessian-vector product of chi2 with the track states
+ * profiled out (each track's refit response removed), at (theta, align):
+ * d_hv = H v, d_v and d_hv double [4S][3].  Accumulated with double atomics
+ * (the last bits may vary from run to run). */
+int ut_align_hvp(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* d_track_hits,
+                 uint32_t n_tracks, const compass_params* p, const float* d_align, const float* d_theta,
+                 const double* d_v, double* d_hv, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,11 @@ def lib():
             _lib.orc_fit32_d.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, P]
             _lib.orc_max_threads.restype = ctypes.c_int
+            _lib.orc_align_chi2.restype = ctypes.c_int
+            _lib.orc_align_chi2.argtypes = [P, P, P, P, ctypes.c_uint32, P, P, P, P, P, P, P, P,
+                                            P, P, P, P]
+            _lib.orc_align_refit.restype = ctypes.c_int
+            _lib.orc_align_refit.argtypes = [P, P, P, P, ctypes.c_uint32, P, P, P, P, P, P, P, P]
         return _lib
 
 
@@ -279,3 +284,42 @@ def run_batch(batch, params, n_threads=0, want_windows=False):
     tr = compass(hits.x, hits.hit_off, batch.n_events, batch.geom, Velo(batch), params,
                  want_windows=want_windows, n_threads=n_threads)
     return hits, tr
+
+
+def align_chi2(hits, track_hits, geom, velo, params, align, theta, grads=True):
+    """Alignment chi2 (double) with its gradient with respect to the track
+    states theta [T,3] = (x, tx, qop) and the per-sector alignment
+    align [4S,3] = (dx, dz, gamma), and the per-sector Gauss-Newton blocks
+    [4S,6].  hits: Hits (decoded, any order); track_hits [T,4] hit indices."""
+    th = np.ascontiguousarray(track_hits, np.int32)
+    T = th.shape[0]
+    al = np.ascontiguousarray(align, np.float64)
+    tt = np.ascontiguousarray(theta, np.float64)
+    c2 = np.zeros(1, np.float64)
+    gt = np.zeros((max(T, 1), 3), np.float64) if grads else None
+    ga = np.zeros((4 * geom.n_sectors, 3), np.float64) if grads else None
+    ha = np.zeros((4 * geom.n_sectors, 6), np.float64) if grads else None
+    g = geom_struct(geom)
+    pp = params_struct(params)
+    vel = [np.ascontiguousarray(a[:T], np.float32) for a in (velo.x, velo.y, velo.tx, velo.ty)]
+    lib().orc_align_chi2(_p(hits.x), _p(hits.sector), _p(hits.layer), _p(th), T, ctypes.byref(g),
+                         *(_p(v) for v in vel), ctypes.byref(pp), _p(al), _p(tt), _p(c2),
+                         _p(gt) if grads else None, _p(ga) if grads else None,
+                         _p(ha) if grads else None)
+    if not grads:
+        return float(c2[0])
+    return float(c2[0]), gt[:T], ga, ha
+
+
+def align_refit(hits, track_hits, geom, velo, params, align):
+    """Per-track refit (double) in the aligned detector: theta [T,3]."""
+    th = np.ascontiguousarray(track_hits, np.int32)
+    T = th.shape[0]
+    out = np.zeros((max(T, 1), 3), np.float64)
+    g = geom_struct(geom)
+    pp = params_struct(params)
+    vel = [np.ascontiguousarray(a[:T], np.float32) for a in (velo.x, velo.y, velo.tx, velo.ty)]
+    lib().orc_align_refit(_p(hits.x), _p(hits.sector), _p(hits.layer), _p(th), T, ctypes.byref(g),
+                          *(_p(v) for v in vel), ctypes.byref(pp), _p(np.ascontiguousarray(align, np.float64)),
+                          _p(out))
+    return out[:T]

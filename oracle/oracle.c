@@ -696,3 +696,141 @@ int orc_fit32_d(const float* d, const int* present, const float* t, const float*
                 float w, float px, float ptx, float* out4) {
     return fit32(d, present, t, f, w, px, ptx, &out4[0], &out4[1], &out4[2], &out4[3]);
 }
+
+/* ------------------------------------------------------------------------
+ * Alignment chi2 and its gradient (double precision).
+ *
+ * The p-kick fit of Sec. III-C with the selected hits held fixed, in a
+ * detector whose sector g (= l*S + s) sits at z_l + dz_g, is shifted by dx_g
+ * along x and has its strips rotated in the plane by gamma_g.  Hit h of a
+ * track with state theta = (x, tx, qop) at z_velo:
+ *   z = z_l + dz_g,  y = y_v + ty_v (z - z_velo),  T = tan(a_l + gamma_g)
+ *   m = u_h + dx_g + y T                (position along x at the track's y)
+ *   r = m - [x + tx (z - z_velo) + k qop (z - z_kink)]
+ * chi2_t = sum_h w r^2 + px (x - x_v)^2 + ptx (tx - tx_v)^2.
+ * Derivatives: dr/dx = -1, dr/dtx = -(z - z_velo), dr/dqop = -k (z - z_kink),
+ * dr/ddx = 1, dr/ddz = ty_v T - tx - k qop, dr/dgamma = y (1 + T^2).
+ * h_align: the Gauss-Newton block sum_h 2 w (dr/da)(dr/da)^T per sector,
+ * entries (xx, xz, xg, zz, zg, gg).
+ * ---------------------------------------------------------------------- */
+int orc_align_chi2(const float* hx, const uint16_t* hsec, const uint8_t* hlay, const int32_t* thit,
+                   uint32_t T, const orc_geom* g, const float* vx, const float* vy, const float* vtx,
+                   const float* vty, const orc_params* p, const double* align, const double* theta,
+                   double* chi2_out, double* g_theta, double* g_align, double* h_align) {
+    const int S = g->S;
+    const double sh = p->sigma_hit, sx = p->sigma_x_prior, st = p->sigma_tx_prior;
+    const double w = 1.0 / (sh * sh), px = 1.0 / (sx * sx), ptx = 1.0 / (st * st);
+    const double k = p->kick_k, zk = p->z_kink, zv = g->z_velo;
+    if (g_align) memset(g_align, 0, sizeof(double) * 4 * S * 3);
+    if (h_align) memset(h_align, 0, sizeof(double) * 4 * S * 6);
+    double total = 0.0;
+    for (uint32_t t = 0; t < T; ++t) {
+        const double x = theta[3 * t], tx = theta[3 * t + 1], qop = theta[3 * t + 2];
+        double chi2 = px * (x - vx[t]) * (x - vx[t]) + ptx * (tx - vtx[t]) * (tx - vtx[t]);
+        double gx = 2.0 * px * (x - vx[t]), gtx = 2.0 * ptx * (tx - vtx[t]), gq = 0.0;
+        for (int l = 0; l < 4; ++l) {
+            const int32_t h = thit[4 * t + l];
+            if (h < 0) continue;
+            const int gi = (int)hlay[h] * S + (int)hsec[h];
+            const double dx = align[3 * gi], dz = align[3 * gi + 1], gam = align[3 * gi + 2];
+            const double z = (double)g->z[hlay[h]] + dz;
+            const double y = (double)vy[t] + (double)vty[t] * (z - zv);
+            const double ta = (double)g->tan_a[hlay[h]], tg = tan(gam);
+            const double Tt = (ta + tg) / (1.0 - ta * tg);
+            const double m = (double)hx[h] + dx + y * Tt;
+            const double r = m - (x + tx * (z - zv) + k * qop * (z - zk));
+            chi2 += w * r * r;
+            gx += 2.0 * w * r * (-1.0);
+            gtx += 2.0 * w * r * (-(z - zv));
+            gq += 2.0 * w * r * (-k * (z - zk));
+            const double da[3] = {1.0, (double)vty[t] * Tt - tx - k * qop, y * (1.0 + Tt * Tt)};
+            if (g_align)
+                for (int i = 0; i < 3; ++i) g_align[3 * gi + i] += 2.0 * w * r * da[i];
+            if (h_align) {
+                double* H = h_align + 6 * gi;
+                H[0] += 2.0 * w * da[0] * da[0];
+                H[1] += 2.0 * w * da[0] * da[1];
+                H[2] += 2.0 * w * da[0] * da[2];
+                H[3] += 2.0 * w * da[1] * da[1];
+                H[4] += 2.0 * w * da[1] * da[2];
+                H[5] += 2.0 * w * da[2] * da[2];
+            }
+        }
+        total += chi2;
+        if (g_theta) {
+            g_theta[3 * t] = gx;
+            g_theta[3 * t + 1] = gtx;
+            g_theta[3 * t + 2] = gq;
+        }
+    }
+    *chi2_out = total;
+    return ORC_OK;
+}
+
+/* Track refit in the aligned detector: the theta minimising chi2_t (the
+ * same least-squares problem, now with a z per hit), solved from the normal
+ * equations by equilibrated Gaussian elimination.  Tracks with fewer than 3
+ * hits keep the VELO state with qop = 0. */
+int orc_align_refit(const float* hx, const uint16_t* hsec, const uint8_t* hlay, const int32_t* thit,
+                    uint32_t T, const orc_geom* g, const float* vx, const float* vy, const float* vtx,
+                    const float* vty, const orc_params* p, const double* align, double* theta) {
+    const int S = g->S;
+    const double sh = p->sigma_hit, sx = p->sigma_x_prior, st = p->sigma_tx_prior;
+    const double w = 1.0 / (sh * sh), px = 1.0 / (sx * sx), ptx = 1.0 / (st * st);
+    const double k = p->kick_k, zk = p->z_kink, zv = g->z_velo;
+    for (uint32_t t = 0; t < T; ++t) {
+        double N[3][4];
+        memset(N, 0, sizeof(N));
+        int n = 0;
+        for (int l = 0; l < 4; ++l) {
+            const int32_t h = thit[4 * t + l];
+            if (h < 0) continue;
+            ++n;
+            const int gi = (int)hlay[h] * S + (int)hsec[h];
+            const double dx = align[3 * gi], dz = align[3 * gi + 1], gam = align[3 * gi + 2];
+            const double z = (double)g->z[hlay[h]] + dz;
+            const double y = (double)vy[t] + (double)vty[t] * (z - zv);
+            const double ta = (double)g->tan_a[hlay[h]], tg = tan(gam);
+            const double Tt = (ta + tg) / (1.0 - ta * tg);
+            const double m = (double)hx[h] + dx + y * Tt;
+            const double gr[3] = {1.0, z - zv, k * (z - zk)};
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) N[i][j] += w * gr[i] * gr[j];
+                N[i][3] += w * gr[i] * m;
+            }
+        }
+        theta[3 * t] = vx[t];
+        theta[3 * t + 1] = vtx[t];
+        theta[3 * t + 2] = 0.0;
+        if (n < 3) continue;
+        N[0][0] += px;
+        N[1][1] += ptx;
+        N[0][3] += px * (double)vx[t];
+        N[1][3] += ptx * (double)vtx[t];
+        double sc[3];
+        for (int i = 0; i < 3; ++i) sc[i] = 1.0 / sqrt(N[i][i]);
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) N[i][j] *= sc[i] * sc[j];
+            N[i][3] *= sc[i];
+        }
+        for (int c = 0; c < 3; ++c) {
+            int pv = c;
+            for (int r = c + 1; r < 3; ++r)
+                if (fabs(N[r][c]) > fabs(N[pv][c])) pv = r;
+            if (pv != c)
+                for (int q = 0; q < 4; ++q) { double tmp = N[c][q]; N[c][q] = N[pv][q]; N[pv][q] = tmp; }
+            for (int r = c + 1; r < 3; ++r) {
+                const double f = N[r][c] / N[c][c];
+                for (int q = c; q < 4; ++q) N[r][q] -= f * N[c][q];
+            }
+        }
+        double sol[3];
+        for (int r = 2; r >= 0; --r) {
+            double s = N[r][3];
+            for (int q = r + 1; q < 3; ++q) s -= N[r][q] * sol[q];
+            sol[r] = s / N[r][r];
+        }
+        for (int i = 0; i < 3; ++i) theta[3 * t + i] = sol[i] * sc[i];
+    }
+    return ORC_OK;
+}

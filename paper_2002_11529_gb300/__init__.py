@@ -25,7 +25,8 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPA
 
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
-           "ut_decode_noalloc", "ut_run_batched")
+           "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
+           "ut_align_refit", "ut_align_hvp")
 
 
 class UtGeometry(ctypes.Structure):
@@ -103,6 +104,10 @@ def lib():
                 "compass_fit": ([P, P, P, U32, P, P, P], I),
                 "ut_decode_noalloc": ([P, P, U64, P, I, P, I, P, P], I),
                 "ut_run_batched": ([P, P, U64, P, I, P, U32, P, P, P, P, P, SZ, P], I),
+                "ut_align_workspace_size": ([I], SZ),
+                "ut_align_chi2": ([P, P, P, P, U32, P, P, P, P, P, P, P, P, SZ, P], I),
+                "ut_align_refit": ([P, P, P, P, U32, P, P, P, P], I),
+                "ut_align_hvp": ([P, P, P, P, U32, P, P, P, P, P, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)

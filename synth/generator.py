@@ -142,7 +142,7 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
              noise_frac: float | None = None, efficiency: float = 0.95,
              backward_frac: float = 0.0, field: float = KICK_K,
              smear: bool = True, plane_covering: bool = False,
-             p_range=(1.5, 100.0), flags_random: bool = True) -> Batch:
+             p_range=(1.5, 100.0), flags_random: bool = True, misalign=None) -> Batch:
     """Generate a seeded batch.
 
     hits: target hits per event (noise = target - signal, at least 0), or
@@ -152,6 +152,9 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
     field: kick constant used to make the hits (0 gives straight tracks).
     plane_covering: VELO x at z=770 drawn so that the tracks cover the plane
     (used by the alignment workload) instead of coming from the beam line.
+    misalign: optional (dx, dz, gamma), each [4, S]: sector (l, s) sits at
+    z_l + dz, shifted by dx along x and its strips rotated by gamma in the
+    plane (strip line x = u + dx + y tan(a_l + gamma)).
     """
     geom = Geometry(n_sectors=n_sectors)
     rng = np.random.Generator(np.random.Philox(key=seed))
@@ -200,12 +203,22 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
     keep = rng.random(4 * T) < efficiency
     smear_v = rng.normal(0.0, sigma, 4 * T) if smear else np.zeros(4 * T)
     flag_v = rng.integers(0, 32, 4 * T) if flags_random else np.zeros(4 * T, np.int64)
+    def measure(zz, dxs, gam):
+        dz = zz - Z_VELO
+        xt = vx[tl_t].astype(np.float64) + vtx[tl_t] * dz + field * qop32[tl_t].astype(np.float64) * (zz - Z_KINK)
+        yt = vy[tl_t].astype(np.float64) + vty[tl_t] * dz
+        ta = (tan_a[tl_l] + np.tan(gam)) / (1.0 - tan_a[tl_l] * np.tan(gam))
+        return xt - dxs - yt * ta + smear_v
+
     zz = z[tl_l]
-    dz = zz - Z_VELO
-    xt = vx[tl_t].astype(np.float64) + vtx[tl_t] * dz + field * qop32[tl_t].astype(np.float64) * (zz - Z_KINK)
-    yt = vy[tl_t].astype(np.float64) + vty[tl_t] * dz
-    u = xt - yt * tan_a[tl_l] + smear_v
+    u = measure(zz, 0.0, 0.0)
     sec = np.floor((u - x_min) / SECTOR_PITCH).astype(np.int64)
+    if misalign is not None:
+        mdx, mdz, mg = (np.asarray(a, np.float64) for a in misalign)
+        for _ in range(2):   # the sector crossed depends on the sector's own offsets
+            sc = np.clip(sec, 0, S - 1)
+            u = measure(zz + mdz[tl_l, sc], mdx[tl_l, sc], mg[tl_l, sc])
+            sec = np.floor((u - x_min) / SECTOR_PITCH).astype(np.int64)
     inside = (sec >= 0) & (sec < S)
     loc = u - (x_min + SECTOR_PITCH * np.clip(sec, 0, S - 1))
     inside &= (loc >= 0.0) & (loc < active)
@@ -323,3 +336,54 @@ def subset(b: Batch, e0: int, e1: int) -> Batch:
         bank_n=b.bank_n[e0 * B: e1 * B], truth_event=b.truth_event[tsl] - e0,
         truth_layer=b.truth_layer[tsl], truth_sector=b.truth_sector[tsl],
         truth_h=b.truth_h[tsl], truth_flags=b.truth_flags[tsl], truth_track=tt)
+
+
+@dataclasses.dataclass
+class AlignmentSet:
+    """Tracks with 3 or 4 true hits in a misaligned detector.
+
+    batch holds the raw banks of all generated tracks; the alignment tracks
+    are the first n_tracks generated tracks with at least 3 hits, given by
+    their VELO state and the raw-order index of their hit in each layer."""
+    batch: Batch
+    dx: np.ndarray          # [4, S] injected offsets (mm)
+    dz: np.ndarray          # [4, S] (mm)
+    gamma: np.ndarray       # [4, S] in-plane rotation (rad)
+    track_hits: np.ndarray  # [T, 4] raw-order hit index per layer, -1 none
+    x: np.ndarray           # [T] VELO state of the alignment tracks
+    y: np.ndarray
+    tx: np.ndarray
+    ty: np.ndarray
+    qop_true: np.ndarray
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.track_hits.shape[0])
+
+    def align_true(self) -> np.ndarray:
+        """[4S, 3] (dx, dz, gamma) per global sector l*S + s."""
+        return np.stack([self.dx.ravel(), self.dz.ravel(), self.gamma.ravel()], 1)
+
+
+def generate_alignment(n_tracks: int = 100_000, n_sectors: int = 256, seed: int = 4,
+                       sigmas=(0.05, 0.2, 1e-4), tracks_per_event: int = 1000,
+                       plane_covering: bool = True) -> AlignmentSet:
+    """Misaligned-detector workload: per-sector (dx, dz, gamma) drawn from
+    N(0, sigmas); noise-free events of plane-covering tracks; the selected
+    hits of each track are its generated hits (held fixed)."""
+    rng = np.random.Generator(np.random.Philox(key=seed + 7919))
+    dx = rng.normal(0.0, sigmas[0], (4, n_sectors))
+    dz = rng.normal(0.0, sigmas[1], (4, n_sectors))
+    gm = rng.normal(0.0, sigmas[2], (4, n_sectors))
+    n_gen = int(n_tracks / 0.95) + tracks_per_event
+    n_events = max(1, (n_gen + tracks_per_event - 1) // tracks_per_event)
+    b = generate(n_events=n_events, n_sectors=n_sectors, tracks=tracks_per_event, hits=None,
+                 noise_frac=0.0, seed=seed, plane_covering=plane_covering,
+                 misalign=(dx, dz, gm))
+    T = b.n_tracks
+    th = np.full((T, 4), -1, np.int64)
+    idx = np.nonzero(b.truth_track >= 0)[0]
+    th[b.truth_track[idx], b.truth_layer[idx].astype(np.int64)] = idx
+    keep = np.nonzero((th >= 0).sum(axis=1) >= 3)[0][:n_tracks]
+    return AlignmentSet(b, dx, dz, gm, th[keep].astype(np.int32), b.velo_x[keep], b.velo_y[keep],
+                        b.velo_tx[keep], b.velo_ty[keep], b.qop_true[keep])
