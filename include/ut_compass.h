@@ -298,6 +298,76 @@ int ut_align_hvp(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, cons
                  uint32_t n_tracks, const compass_params* p, const float* d_align, const float* d_theta,
                  const double* d_v, double* d_hv, void* stream);
 
+/*
+ * Serving engine: continuous batching of whole-path requests under a fixed
+ * device-memory budget (the paper's multi-stream host framework, Sec. I,
+ * as a request loop).  The engine owns one device arena of budget_bytes and
+ * n_slots CUDA streams (each with its own context and status word).  A
+ * worker thread admits waiting requests in arrival order as soon as a slot
+ * is idle and the arena can hold the request's buffers; an admitted
+ * request's copies in, its ut_run_batched launch and its copies out run on
+ * the slot's stream, overlapping with the other slots.  Its arena block is
+ * freed when its completion event fires.
+ */
+typedef struct ut_server ut_server;
+
+/* One request: HOST buffers (page-locked for asynchronous copies), owned by
+ * the caller and kept alive until the request has completed.  Inputs as in
+ * ut_decode / compass_find; outputs: the track slots (any may be NULL). */
+typedef struct ut_server_request {
+    const uint32_t* raw;
+    uint64_t n_raw_words;
+    const uint64_t* ev_off;       /* n_events + 1 */
+    int n_events;                 /* >= 1 */
+    const float* vx;
+    const float* vy;
+    const float* vtx;
+    const float* vty;
+    const uint8_t* flags;
+    const uint32_t* trk_off;      /* n_events + 1 */
+    uint32_t n_tracks;
+    int32_t* out_hit;             /* [n_tracks][4] */
+    float* out_qop;
+    float* out_chi2;
+    float* out_x;
+    float* out_tx;
+    uint8_t* out_nhits;
+    uint8_t* out_found;
+} ut_server_request;
+
+typedef struct ut_server_result {
+    int64_t id;                   /* as returned by ut_server_submit */
+    int status;                   /* UT_OK or the request's device error   */
+    int64_t where_a, where_b;     /* error location (as ut_status)         */
+    double queue_s;               /* submission to admission (s)           */
+    double latency_s;             /* submission to completion (s)          */
+    int slot;                     /* stream slot it ran on                 */
+} ut_server_result;
+
+/* Arena bytes one request needs. */
+size_t ut_server_request_bytes(const ut_geometry* geom, const ut_server_request* r);
+
+/* Create an engine on the current device (allocates the arena, the streams
+ * and the worker thread).  cfg: launch shape of the batched kernel (NULL =
+ * defaults). */
+int ut_server_create(ut_server** sv, const ut_geometry* geom, const compass_params* p, size_t budget_bytes,
+                     int n_slots, const ut_launch_config* cfg);
+
+/* Queue a request; returns its id (>= 0) or UT_ERR_ARG, or UT_ERR_CAPACITY
+ * if it can never fit the arena.  Thread-safe. */
+int64_t ut_server_submit(ut_server* sv, const ut_server_request* r);
+
+/* Move up to max_results completed requests into results (oldest first);
+ * wait != 0 blocks until at least one has completed or none is in flight.
+ * Returns how many were written. */
+int ut_server_poll(ut_server* sv, ut_server_result* results, int max_results, int wait);
+
+/* Requests queued or running; arena bytes in use and the peak so far. */
+int ut_server_stats(ut_server* sv, int64_t* in_flight, size_t* arena_used, size_t* arena_peak);
+
+/* Finish every queued request, then free the engine. */
+int ut_server_destroy(ut_server* sv);
+
 #ifdef __cplusplus
 }
 #endif
