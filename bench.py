@@ -43,12 +43,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
-    ap.add_argument("--form", default="batched", choices=["batched", "fused", "plain"])
+    ap.add_argument("--form", default="fused", choices=["batched", "fused", "plain"])
     ap.add_argument("--autotune", action="store_true", help="pick the batched launch shape by a sweep")
     ap.add_argument("--x-cap", type=int, default=8192)
     ap.add_argument("--tracks-per-warp", type=int, default=4)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the uneven-workload form comparison and the serving measurement")
     return ap.parse_args()
 
 
@@ -175,6 +177,78 @@ def run_reference(args):
                              "sample": f"first {sample_events} events of the workload per step"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_forms_on_uneven_workload(g, params, flush, steps=5):
+    """North-star comparison on the 20000-event uneven workload: the batched
+    persistent form (one graph-replayed launch, autotuned shape) against
+    the plain per-kernel form (decode, sort, find, fit)."""
+    import torch
+    batch = make_batch("batched", 0)
+    ctx = g.Context(batch.geom)
+    pipe = g.Pipeline(ctx, batch, params)
+    from paper_2002_11529_gb300 import autotune
+    cfg, _ = autotune.autotune(pipe, reps=2, flush=flush)
+    runner = g.GraphRunner(pipe, cfg)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            flush.zero_()
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    ms_b = timed(runner.replay)
+    ms_p = timed(lambda: pipe.run_plain(stream, cfg.tracks_per_warp, 256))
+    ctx.check(stream, "uneven workload")
+    E = batch.n_events
+    out = {"workload": f"{E} events, hits/event lognormal (median 3000, sigma 0.6, 500-15000), "
+                       f"tracks/event 0.05*hits, 4x256 sectors",
+           "batched_form": {"ms": round(ms_b, 4), "events_per_s": E / ms_b * 1e3,
+                            "launch": {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block,
+                                       "graph": True, "kernels_per_step": 1}},
+           "plain_form": {"ms": round(ms_p, 4), "events_per_s": E / ms_p * 1e3, "kernels_per_step": 4},
+           "batched_over_plain": ms_p / ms_b}
+    ctx.close()
+    return out
+
+
+def measure_serving(g, params, loads=(0.5, 0.8, 0.95)):
+    """Serving: requests of 64-4096 events (log-uniform, plain-workload
+    occupancy) through the continuous-batching engine, 40 GB budget,
+    8 stream slots: sustained peak (all submitted at once), then Poisson
+    arrivals at fractions of that peak; p50/p99 request latency."""
+    import numpy as np
+    import synth
+    from paper_2002_11529_gb300 import serve
+    rng = np.random.default_rng(55)
+    sizes = np.exp(rng.uniform(np.log(64), np.log(4096), 24)).astype(int)
+    batches = [synth.generate(n_events=int(n), n_sectors=256, tracks=200, hits=4000, seed=7000 + i)
+               for i, n in enumerate(sizes)]
+    reqs = [serve.HostRequest.from_batch(b) for b in batches]
+    res = {"requests_per_level": 2 * len(reqs), "events_per_request": "64-4096 log-uniform",
+           "budget_bytes": 40 << 30, "slots": 8}
+    with serve.Server(batches[0].geom, params, budget_bytes=40 << 30, n_slots=8) as sv:
+        serve.run_closed_loop(sv, reqs)            # warm-up
+        peak, _ = serve.run_closed_loop(sv, reqs + reqs)
+        res["peak_events_per_s"] = peak["events_per_s"]
+        res["peak_p99_ms"] = peak["p99_ms"]
+        for f in loads:
+            summ, _ = serve.run_open_loop(sv, reqs + reqs, events_per_s=f * peak["events_per_s"], seed=int(f * 100))
+            res[f"load_{int(round(f * 100))}"] = {k: summ[k] for k in ("events_per_s", "p50_ms", "p99_ms",
+                                                                       "queue_p50_ms", "errors")}
+        res["arena_peak_bytes"] = sv.stats()["arena_peak"]
+    return res
 
 
 def algorithmic_bytes(batch):
@@ -381,6 +455,9 @@ def main():
         "clocks": clk,
         "wall_s": wall,
     }
+    if not args.no_variants and world == 1:
+        line["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
+        line["serving"] = measure_serving(g, params)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
     print(json.dumps(line), flush=True)
