@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
     sm.mbar = &mbar;
     sm.s_base = &s_base;
     sm.warp_tot = warp_tot;
+    sm.bmap = nullptr;      // per-hit path: shared memory holds the event's x for the search
+    sm.srcmap = nullptr;
     float* sx = reinterpret_cast<float*>(smem + L.sx_byte0);
     GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.heads_byte0);
 
@@ -174,6 +176,8 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     D.status = ctx->d_status;
     D.stage_words = (uint32_t)stage_words;
+    D.map_cap = 0;
+    D.vec_ok = 0;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
     switch (tpw) {
         case 1: return launch_batched_g<32>(D, A, block, ctx->num_sms, st);

@@ -41,6 +41,10 @@ __global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeA
     sm.mbar = &mbar;
     sm.s_base = &s_base;
     sm.warp_tot = warp_tot;
+    // bank of every hit, and for the sorted decode the source of every
+    // output position (events of at most map_cap hits)
+    sm.bmap = a.map_cap ? reinterpret_cast<uint16_t*>(smem + stage_byte0 + (size_t)a.stage_words * 4) : nullptr;
+    sm.srcmap = SORT && sm.bmap ? sm.bmap + a.map_cap : nullptr;
 
     if (tid == 0) {
         s_event = (int)atomicAdd(a.ticket, 1u);
@@ -162,9 +166,15 @@ __global__ void __launch_bounds__(kDecodeThreads) ut_sort_kernel(const SortArgs 
     }
 }
 
-static size_t decode_smem_bytes(int B, bool sort, uint32_t stage_words) {
+static size_t decode_smem_bytes(int B, bool sort, uint32_t stage_words, uint32_t map_cap) {
     const size_t head = (size_t)((sort ? kBigWarps * kKeyBins : 0) + B + 1) * 4 + 16;
-    return head + (size_t)stage_words * 4;
+    return head + (size_t)stage_words * 4 + (size_t)map_cap * (sort ? 2 : 1) * sizeof(uint16_t);
+}
+
+static int outputs_aligned(const ut_hits* h) {
+    const uintptr_t m = (uintptr_t)h->x | (uintptr_t)h->z | (uintptr_t)h->sector | (uintptr_t)h->layer |
+                        (uintptr_t)h->id;
+    return (m & 15u) == 0;
 }
 
 }  // namespace utc
@@ -209,8 +219,10 @@ extern "C" int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_word
     a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     a.status = ctx->d_status;
     a.stage_words = kStageWordsDefault;
+    a.map_cap = B <= 65536 ? kMapCapDefault : 0;
+    a.vec_ok = outputs_aligned(out);
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
-    const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words);
+    const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words, a.map_cap);
     cudaError_t err;
     if (sorted) {
         err = cudaFuncSetAttribute(ut_decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -326,11 +338,13 @@ extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw,
     a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 16);
     a.status = d_status;
     a.stage_words = kStageWordsDefault;
+    a.map_cap = B <= 65536 ? kMapCapDefault : 0;
+    a.vec_ok = outputs_aligned(out);
     // the array keeps the previous call's contents: clear the counter and the
     // look-back state of the events used here
     if (cudaMemsetAsync(scratch, 0, 16 + (size_t)n_events * sizeof(unsigned long long), st) != cudaSuccess)
         return UT_ERR_CUDA;
-    const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words);
+    const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words, a.map_cap);
     cudaError_t err;
     if (sorted) {
         err = cudaFuncSetAttribute(ut_decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -17,9 +17,10 @@ namespace utc {
 
 constexpr int kMaxDecodeThreads = 512;
 constexpr int kSmallBank = 64;          // banks up to this size rank by direct counting
-constexpr int kBigWarps = 2;            // warps that sort larger banks
+constexpr int kBigWarps = 1;            // warps that sort larger banks
 constexpr int kKeyBins = 1024;          // half-strip keys (strips <= 512)
 constexpr uint32_t kStageWordsDefault = 8192;
+constexpr uint32_t kMapCapDefault = 8192;
 
 // Tile (event) state of the look-back, 64-bit: flag in bits 62-63.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
@@ -46,6 +47,8 @@ struct DecodeArgs {
     unsigned long long* tile_state;
     unsigned long long* status;
     uint32_t stage_words;
+    uint32_t map_cap;            // events up to this many hits use the mapped, vector-store path
+    int vec_ok;                  // output arrays are 16-byte aligned
 };
 
 struct HitOut {
@@ -56,15 +59,25 @@ struct HitOut {
     uint32_t* id;
 };
 
-// Decoded hit parameters of word w in sector s of layer l (Sec. IV):
-// x = x0_s + (h + 1/2) * pitch/2 with x0_s = s * sector_pitch + x_min.
-// Each float operation is a separate IEEE op (no contraction: -fmad=false).
-__device__ __forceinline__ void write_hit(const DecodeArgs& a, uint32_t o, int l, int s, uint32_t w, float* sx,
-                                          uint32_t sx_cap, uint32_t local) {
+// Layer l and sector s of bank b = l * S + s, by comparison (no division).
+__device__ __forceinline__ void bank_ls(int b, int S, int& l, int& s) {
+    l = (int)(b >= S) + (int)(b >= 2 * S) + (int)(b >= 3 * S);
+    s = b - l * S;
+}
+
+// x at y = 0 of hit word w in sector s (Sec. IV): x0_s + (h + 1/2) pitch/2,
+// x0_s = s * sector_pitch + x_min.  Each float operation is a separate IEEE
+// op (no contraction: -fmad=false).
+__device__ __forceinline__ float decode_x(const DecodeArgs& a, int s, uint32_t w) {
     const uint32_t h = half_strip(w);
     const float x0 = __fadd_rn(__fmul_rn((float)s, a.sector_pitch), a.x_min);
     const float c = __fmul_rn(__fadd_rn((float)h, 0.5f), a.half_pitch);
-    const float x = __fadd_rn(x0, c);
+    return __fadd_rn(x0, c);
+}
+
+__device__ __forceinline__ void write_hit(const DecodeArgs& a, uint32_t o, int l, int s, uint32_t w, float* sx,
+                                          uint32_t sx_cap, uint32_t local) {
+    const float x = decode_x(a, s, w);
     a.x[o] = x;
     if (sx != nullptr && local < sx_cap) sx[local] = x;
     a.z[o] = a.zl[l];
@@ -163,7 +176,166 @@ struct DecodeSmem {
     uint64_t* mbar;              // bulk-copy barrier (initialised by the caller)
     unsigned long long* s_base;  // global hit base of the event
     uint32_t* warp_tot;          // kMaxDecodeThreads / 32
+    uint16_t* bmap;              // map_cap: bank of each hit (null: mapped path off)
+    uint16_t* srcmap;            // map_cap: hit written at each output position
 };
+
+__device__ __forceinline__ const uint16_t* bank_words(const uint32_t* evw, int b) {
+    return reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
+}
+
+// Ranks the hits of banks of more than kSmallBank hits by a counting sort
+// on the half-strip key, one warp per bank (histogram, exclusive scan of the
+// bins, then a stable pass in word order where equal keys inside a 32-word
+// chunk are ranked with a match mask).  place(b, pos, k, w): word k of bank
+// b goes to position pos of the bank.
+template <class Place>
+__device__ void rank_big_banks(const uint32_t* off, int B, const uint32_t* evw, uint32_t* bigcnt, Place place) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    if (wid >= kBigWarps) return;
+    uint32_t* cnt = bigcnt + wid * kKeyBins;
+    for (int b0 = wid * 32; b0 < B; b0 += kBigWarps * 32) {
+        const int bl = b0 + lane;
+        const bool big = bl < B && (off[bl + 1] - off[bl]) > (uint32_t)kSmallBank;
+        uint32_t mask = __ballot_sync(0xffffffffu, big);
+        while (mask) {
+            const int b = b0 + __ffs(mask) - 1;
+            mask &= mask - 1;
+            const uint32_t n = off[b + 1] - off[b];
+            const uint16_t* w16 = bank_words(evw, b);
+            for (int q = lane; q < kKeyBins; q += 32) cnt[q] = 0;
+            __syncwarp();
+            for (uint32_t k = lane; k < n; k += 32)
+                atomicAdd(&cnt[min(half_strip(w16[k]), (uint32_t)(kKeyBins - 1))], 1u);
+            __syncwarp();
+            uint32_t run = 0;
+            for (int q = 0; q < kKeyBins / 32; ++q) run += cnt[lane * (kKeyBins / 32) + q];
+            uint32_t incl = run;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            uint32_t acc = incl - run;
+            for (int q = 0; q < kKeyBins / 32; ++q) {
+                const uint32_t c = cnt[lane * (kKeyBins / 32) + q];
+                cnt[lane * (kKeyBins / 32) + q] = acc;
+                acc += c;
+            }
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < n; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                const bool valid = k < n;
+                const uint32_t w = valid ? w16[k] : 0u;
+                const uint32_t hk = valid ? min(half_strip(w), (uint32_t)(kKeyBins - 1)) : kKeyBins + lane;
+                const uint32_t peers = __match_any_sync(0xffffffffu, hk);
+                const uint32_t before = __popc(peers & lanemask_lt());
+                const uint32_t pos = valid ? cnt[hk] + before : 0u;
+                __syncwarp();
+                if (valid && before == 0) cnt[hk] += __popc(peers);
+                __syncwarp();
+                if (valid) place(b, pos, k, w);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Decoded hit of output position o (event-local) whose word is w in bank b.
+struct DecodedHit {
+    float x, z;
+    uint32_t s, l, id;
+};
+
+__device__ __forceinline__ DecodedHit decoded_hit(const DecodeArgs& a, int b, uint32_t w) {
+    int l, s;
+    bank_ls(b, a.S, l, s);
+    DecodedHit h;
+    h.x = decode_x(a, s, w);
+    h.z = a.zl[l];
+    h.s = (uint32_t)s;
+    h.l = (uint32_t)l;
+    h.id = ((uint32_t)l << 24) | ((uint32_t)s << 16) | w;
+    return h;
+}
+
+// The decode of an event of at most map_cap hits (after the offsets and the
+// global base are known).  bmap[i] = bank of event-local hit i, filled by
+// one thread per bank.  SORT: the stable rank r of every hit of a bank of at
+// most kSmallBank hits is the number of hits of the bank with a smaller
+// (half-strip, word index) key, and srcmap[off[b] + r] = i (larger banks by
+// rank_big_banks).  Then the outputs are produced in output order; groups of
+// four outputs that start on a 16-byte boundary in global memory are written
+// with vector stores.
+template <bool SORT>
+__device__ void decode_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, const uint32_t* evw,
+                              unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int B = 4 * a.S;
+    const uint32_t* off = sm.off;
+    uint16_t* bmap = sm.bmap;
+    uint16_t* srcm = sm.srcmap;
+    for (int b = tid; b < B; b += nt) {
+        const uint32_t j1 = off[b + 1];
+        for (uint32_t j = off[b]; j < j1; ++j) bmap[j] = (uint16_t)b;
+    }
+    __syncthreads();
+    if (SORT) {
+        for (uint32_t i = tid; i < total; i += nt) {
+            const int b = bmap[i];
+            const uint32_t o0 = off[b], n = off[b + 1] - o0;
+            if (n > (uint32_t)kSmallBank) continue;
+            const uint16_t* w16 = bank_words(evw, b);
+            const uint32_t k = i - o0;
+            const uint32_t key = (half_strip(w16[k]) << 16) | k;
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < n; ++j) r += ((half_strip(w16[j]) << 16) | j) < key;
+            srcm[o0 + r] = (uint16_t)i;
+        }
+        rank_big_banks(off, B, evw, sm.bigcnt,
+                       [&](int b, uint32_t pos, uint32_t k, uint32_t) { srcm[off[b] + pos] = (uint16_t)(off[b] + k); });
+        __syncthreads();
+    }
+    auto hit_at = [&](uint32_t o) -> DecodedHit {
+        const int b = bmap[o];
+        const uint32_t i = SORT ? (uint32_t)srcm[o] : o;
+        const uint32_t w = bank_words(evw, b)[i - off[b]];
+        if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
+        return decoded_hit(a, b, w);
+    };
+    auto one = [&](uint32_t o) {
+        const DecodedHit h = hit_at(o);
+        if (sx != nullptr && o < sx_cap) sx[o] = h.x;
+        if (!fits) return;
+        const size_t g = (size_t)(base + o);
+        a.x[g] = h.x;
+        a.z[g] = h.z;
+        a.sector[g] = (uint16_t)h.s;
+        a.layer[g] = (uint8_t)h.l;
+        a.id[g] = h.id;
+    };
+    uint32_t head = a.vec_ok ? (uint32_t)((4u - (uint32_t)(base & 3u)) & 3u) : total;
+    if (head > total) head = total;
+    const uint32_t nq = (total - head) / 4;
+    for (uint32_t o = tid; o < head; o += nt) one(o);
+    for (uint32_t q = tid; q < nq; q += nt) {
+        const uint32_t o = head + 4 * q;
+        DecodedHit h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h[j] = hit_at(o + j);
+            if (sx != nullptr && o + j < sx_cap) sx[o + j] = h[j].x;
+        }
+        if (!fits) continue;
+        const size_t g = (size_t)(base + o);
+        *reinterpret_cast<float4*>(a.x + g) = make_float4(h[0].x, h[1].x, h[2].x, h[3].x);
+        *reinterpret_cast<float4*>(a.z + g) = make_float4(h[0].z, h[1].z, h[2].z, h[3].z);
+        *reinterpret_cast<uint2*>(a.sector + g) = make_uint2(h[0].s | (h[1].s << 16), h[2].s | (h[3].s << 16));
+        *reinterpret_cast<uint32_t*>(a.layer + g) = h[0].l | (h[1].l << 8) | (h[2].l << 16) | (h[3].l << 24);
+        *reinterpret_cast<uint4*>(a.id + g) = make_uint4(h[0].id, h[1].id, h[2].id, h[3].id);
+    }
+    for (uint32_t o = head + 4 * nq + tid; o < total; o += nt) one(o);
+}
 
 // Decode event e with the whole block.  `phase` is the parity of the bulk
 // copy barrier's next phase (toggled when a copy completes); `tma_ok` turns
@@ -262,12 +434,18 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     if (e == a.n_events - 1 && tid == 0) a.hit_off[(size_t)a.n_events * B] = (uint32_t)end;
     if (!ev_ok) return;
 
-    // Decode: one thread per hit of the event (bank found by binary search).
+    // Decode.  Events of at most map_cap hits take the mapped path; larger
+    // ones use one thread per hit (bank by binary search) writing at its
+    // ranked slot.
+    if (sm.bmap != nullptr && total <= a.map_cap) {
+        decode_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap);
+        return;
+    }
     for (uint32_t i = tid; i < total; i += nt) {
         const int b = find_bank(off, B, i);
         const uint32_t k = i - off[b];
         const uint32_t n = off[b + 1] - off[b];
-        const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
+        const uint16_t* w16 = bank_words(evw, b);
         const uint32_t w = w16[k];
         if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
         uint32_t r = k;
@@ -276,64 +454,18 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
             const uint32_t hk = min(half_strip(w), (uint32_t)(kKeyBins - 1));
             r = rank_small(w16, n, k, hk);
         }
-        if (fits) write_hit(a, (uint32_t)(base + off[b] + r), b / S, b % S, w, sx, sx_cap, off[b] + r);
-    }
-
-    if (SORT) {
-        // Larger banks: counting sort on the half-strip key by one warp per
-        // bank (histogram, exclusive scan of the bins, then a stable pass in
-        // word order where equal keys inside a 32-word chunk are ranked with
-        // a match mask).
-        const int wid = tid >> 5, lane = tid & 31;
-        if (wid < kBigWarps) {
-            uint32_t* cnt = sm.bigcnt + wid * kKeyBins;
-            for (int b0 = wid * 32; b0 < B; b0 += kBigWarps * 32) {
-                const int bl = b0 + lane;
-                const bool big = bl < B && (off[bl + 1] - off[bl]) > (uint32_t)kSmallBank;
-                uint32_t mask = __ballot_sync(0xffffffffu, big);
-                while (mask) {
-                    const int b = b0 + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const uint32_t n = off[b + 1] - off[b];
-                    const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
-                    for (int q = lane; q < kKeyBins; q += 32) cnt[q] = 0;
-                    __syncwarp();
-                    for (uint32_t k = lane; k < n; k += 32)
-                        atomicAdd(&cnt[min(half_strip(w16[k]), (uint32_t)(kKeyBins - 1))], 1u);
-                    __syncwarp();
-                    uint32_t run = 0;
-                    for (int q = 0; q < kKeyBins / 32; ++q) run += cnt[lane * (kKeyBins / 32) + q];
-                    uint32_t incl = run;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
-                        if (lane >= d) incl += t;
-                    }
-                    uint32_t acc = incl - run;
-                    for (int q = 0; q < kKeyBins / 32; ++q) {
-                        const uint32_t c = cnt[lane * (kKeyBins / 32) + q];
-                        cnt[lane * (kKeyBins / 32) + q] = acc;
-                        acc += c;
-                    }
-                    __syncwarp();
-                    for (uint32_t k0 = 0; k0 < n; k0 += 32) {
-                        const uint32_t k = k0 + lane;
-                        const bool valid = k < n;
-                        const uint32_t w = valid ? w16[k] : 0u;
-                        const uint32_t hk = valid ? min(half_strip(w), (uint32_t)(kKeyBins - 1)) : kKeyBins + lane;
-                        const uint32_t peers = __match_any_sync(0xffffffffu, hk);
-                        const uint32_t before = __popc(peers & lanemask_lt());
-                        const uint32_t pos = valid ? cnt[hk] + before : 0u;
-                        __syncwarp();
-                        if (valid && before == 0) cnt[hk] += __popc(peers);
-                        __syncwarp();
-                        if (valid && fits) write_hit(a, (uint32_t)(base + off[b] + pos), b / S, b % S, w, sx, sx_cap, off[b] + pos);
-                    }
-                    __syncwarp();
-                }
-            }
+        if (fits) {
+            int l, s;
+            bank_ls(b, S, l, s);
+            write_hit(a, (uint32_t)(base + off[b] + r), l, s, w, sx, sx_cap, off[b] + r);
         }
     }
+    if (SORT && fits)
+        rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t, uint32_t w) {
+            int l, s;
+            bank_ls(b, S, l, s);
+            write_hit(a, (uint32_t)(base + off[b] + pos), l, s, w, sx, sx_cap, off[b] + pos);
+        });
 }
 
 }  // namespace utc
