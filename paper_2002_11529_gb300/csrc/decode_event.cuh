@@ -86,8 +86,9 @@ __device__ __forceinline__ void write_hit(const DecodeArgs& a, uint32_t o, int l
     a.id[o] = ((uint32_t)l << 24) | ((uint32_t)s << 16) | w;
 }
 
-// Block-wide exclusive scan of cnt[0..n) in place; returns the total.
-// n may exceed the block size (each thread scans a contiguous run).
+// Block-wide exclusive scan of cnt[0..n) in place, cnt[n] = total; returns
+// the total.  n may exceed the block size (each thread scans a contiguous
+// run).  Ends with a barrier: every thread may read cnt[0..n] on return.
 static __device__ uint32_t block_exclusive_scan(uint32_t* cnt, int n, uint32_t* warp_tot) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int per = (n + nt - 1) / nt;
@@ -122,37 +123,65 @@ static __device__ uint32_t block_exclusive_scan(uint32_t* cnt, int n, uint32_t* 
         cnt[b] = run;
         run += c;
     }
+    if (tid == 0) cnt[n] = total;
     __syncthreads();
     return total;
 }
 
 // Decoupled look-back (single-pass prefix sum across events): returns the
-// sum of the aggregates of all events before `e`.  Executed by one warp.
+// sum of the aggregates of all events before `e`.  Executed by one warp;
+// each step reads the states of 128 predecessors (four per lane, lane-major
+// by distance) and waits only for those nearer than the nearest inclusive
+// prefix.
 static __device__ unsigned long long lookback(unsigned long long* tile_state, int e, unsigned long long* status) {
     const int lane = threadIdx.x & 31;
     unsigned long long excl = 0;
-    int j = e - 1;
+    int j = e - 1;  // nearest predecessor not yet summed
     long long spins = 0;
     while (j >= 0) {
-        const int idx = j - lane;
-        unsigned long long s = idx >= 0 ? ld_volatile_u64(tile_state + idx) : kFlagPrefix;
-        // wait until every lane sees a published state
-        while (__any_sync(0xffffffffu, (s >> 62) == 0)) {
+        unsigned long long st[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int idx = j - (lane * 4 + t);
+            st[t] = idx >= 0 ? ld_volatile_u64(tile_state + idx) : kFlagPrefix;
+        }
+        int tp;
+        uint32_t pmask;
+        int stop;
+        for (;;) {
+            tp = 4;
+#pragma unroll
+            for (int t = 3; t >= 0; --t)
+                if ((st[t] >> 62) == 2) tp = t;
+            pmask = __ballot_sync(0xffffffffu, tp < 4);
+            stop = pmask ? __ffs(pmask) - 1 : 32;  // lane holding the nearest prefix
+            bool missing = false;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool needed = lane < stop || (lane == stop && t < tp);
+                missing |= needed && (st[t] >> 62) == 0;
+            }
+            if (!__any_sync(0xffffffffu, missing)) break;
             if (++spins > kSpinLimit) {
                 if (lane == 0) report(status, UT_ERR_TIMEOUT, e, -1);
                 return excl;
             }
             __nanosleep(32);
-            if ((s >> 62) == 0) s = ld_volatile_u64(tile_state + idx);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int idx = j - (lane * 4 + t);
+                if (idx >= 0 && (st[t] >> 62) == 0) st[t] = ld_volatile_u64(tile_state + idx);
+            }
         }
-        const uint32_t pmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-        const int stop = pmask ? __ffs(pmask) - 1 : 31;   // lanes 0..stop contribute
-        unsigned long long v = lane <= stop ? (s & kValueMask) : 0ull;
+        unsigned long long v = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (lane < stop || (lane == stop && t <= tp)) v += st[t] & kValueMask;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
         excl += v;
         if (pmask) break;
-        j -= 32;
+        j -= 128;
     }
     return excl;
 }
@@ -259,47 +288,83 @@ __device__ __forceinline__ DecodedHit decoded_hit(const DecodeArgs& a, int b, ui
     return h;
 }
 
-// The decode of an event of at most map_cap hits (after the offsets and the
-// global base are known).  bmap[i] = bank of event-local hit i, filled by
-// one thread per bank.  SORT: the stable rank r of every hit of a bank of at
-// most kSmallBank hits is the number of hits of the bank with a smaller
-// (half-strip, word index) key, and srcmap[off[b] + r] = i (larger banks by
-// rank_big_banks).  Then the outputs are produced in output order; groups of
-// four outputs that start on a 16-byte boundary in global memory are written
-// with vector stores.
+// Shared-memory maps of an event of at most map_cap hits, built before its
+// global base is known.  bmap[i] = bank of event-local hit i (filled by one
+// thread per bank).  SORT (B <= 1024): key[i] = (half-strip << 6) | word
+// index for banks of at most kSmallBank hits; the stable rank r of such a
+// hit is the number of keys of its bank below its own, kept in bits 10-15
+// of bmap[i].  Then srcmap[off[b] + r] = position of the hit's word in the
+// event's 16-bit words.  The key array occupies srcmap until the ranks are
+// taken.  Larger banks are ranked by rank_big_banks straight into srcmap.
 template <bool SORT>
-__device__ void decode_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, const uint32_t* evw,
-                              unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap) {
+__device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int B = 4 * a.S;
     const uint32_t* off = sm.off;
     uint16_t* bmap = sm.bmap;
     uint16_t* srcm = sm.srcmap;
+    auto key_of = [](uint32_t w, uint32_t k) {
+        return (uint16_t)((min(half_strip(w), (uint32_t)(kKeyBins - 1)) << 6) | k);
+    };
     for (int b = tid; b < B; b += nt) {
-        const uint32_t j1 = off[b + 1];
-        for (uint32_t j = off[b]; j < j1; ++j) bmap[j] = (uint16_t)b;
+        const uint32_t j0 = off[b], n = off[b + 1] - j0;
+        if (SORT && n <= (uint32_t)kSmallBank) {
+            const uint32_t* w32 = evw + evw[b] + 1;  // two words per u32, low half first
+            for (uint32_t k = 0; k < n; k += 2) {
+                const uint32_t v = w32[k >> 1];
+                bmap[j0 + k] = (uint16_t)b;
+                srcm[j0 + k] = key_of(v & 0xFFFFu, k);
+                if (k + 1 < n) {
+                    bmap[j0 + k + 1] = (uint16_t)b;
+                    srcm[j0 + k + 1] = key_of(v >> 16, k + 1);
+                }
+            }
+        } else {
+            for (uint32_t j = j0; j < j0 + n; ++j) bmap[j] = (uint16_t)b;
+        }
     }
     __syncthreads();
-    if (SORT) {
-        for (uint32_t i = tid; i < total; i += nt) {
-            const int b = bmap[i];
-            const uint32_t o0 = off[b], n = off[b + 1] - o0;
-            if (n > (uint32_t)kSmallBank) continue;
-            const uint16_t* w16 = bank_words(evw, b);
-            const uint32_t k = i - o0;
-            const uint32_t key = (half_strip(w16[k]) << 16) | k;
-            uint32_t r = 0;
-            for (uint32_t j = 0; j < n; ++j) r += ((half_strip(w16[j]) << 16) | j) < key;
-            srcm[o0 + r] = (uint16_t)i;
-        }
-        rank_big_banks(off, B, evw, sm.bigcnt,
-                       [&](int b, uint32_t pos, uint32_t k, uint32_t) { srcm[off[b] + pos] = (uint16_t)(off[b] + k); });
-        __syncthreads();
+    if (!SORT) return;
+    for (uint32_t i = tid; i < total; i += nt) {
+        const int b = bmap[i];
+        const uint32_t o0 = off[b], n = off[b + 1] - o0;
+        if (n > (uint32_t)kSmallBank) continue;
+        const uint32_t key = srcm[i];
+        const uint16_t* K = srcm + o0;
+        uint32_t r = 0, j = 0;
+        for (; j + 4 <= n; j += 4)
+            r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
+                 (uint32_t)(K[j + 3] < key);
+        for (; j < n; ++j) r += (uint32_t)(K[j] < key);
+        bmap[i] = (uint16_t)(b | (r << 10));
     }
+    rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
+        srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
+    });
+    __syncthreads();
+    for (uint32_t i = tid; i < total; i += nt) {
+        const uint32_t v = bmap[i];
+        const int b = (int)(v & 0x3FFu);
+        const uint32_t o0 = off[b];
+        if (off[b + 1] - o0 > (uint32_t)kSmallBank) continue;
+        srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
+    }
+    __syncthreads();
+}
+
+// Writes of a mapped event in output order; groups of four outputs that
+// start on a 16-byte boundary in global memory use vector stores.
+template <bool SORT>
+__device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, const uint32_t* evw,
+                             unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t* off = sm.off;
+    const uint16_t* bmap = sm.bmap;
+    const uint16_t* srcm = sm.srcmap;
     auto hit_at = [&](uint32_t o) -> DecodedHit {
-        const int b = bmap[o];
-        const uint32_t i = SORT ? (uint32_t)srcm[o] : o;
-        const uint32_t w = bank_words(evw, b)[i - off[b]];
+        const int b = SORT ? (int)(bmap[o] & 0x3FFu) : (int)bmap[o];
+        const uint32_t w = SORT ? (uint32_t)reinterpret_cast<const uint16_t*>(evw)[srcm[o]]
+                                : (uint32_t)bank_words(evw, b)[o - off[b]];
         if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
         return decoded_hit(a, b, w);
     };
@@ -409,15 +474,17 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     }
     __syncthreads();
     const uint32_t total = block_exclusive_scan(off, B, sm.warp_tot);
-    if (tid == 0) off[B] = total;
 
-    // Global base of this event: publish the aggregate, look back, publish
-    // the inclusive prefix.
+    // Publish the aggregate at once; look back only after the event's own
+    // shared-memory maps are built, so that the predecessors have had the
+    // time to publish theirs.
+    if (tid == 0)
+        st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
+    // (sorted: bank and rank share 16 bits, word positions fit 16 bits)
+    const bool mapped = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
+    if (mapped) map_event<SORT>(a, sm, evw, total);
     if (tid < 32) {
-        if (tid == 0) {
-            st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
-        }
-        unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
+        const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
         if (tid == 0) {
             if (e > 0) st_volatile_u64(a.tile_state + e, kFlagPrefix | ((excl + total) & kValueMask));
             *sm.s_base = excl;
@@ -434,11 +501,10 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     if (e == a.n_events - 1 && tid == 0) a.hit_off[(size_t)a.n_events * B] = (uint32_t)end;
     if (!ev_ok) return;
 
-    // Decode.  Events of at most map_cap hits take the mapped path; larger
-    // ones use one thread per hit (bank by binary search) writing at its
-    // ranked slot.
-    if (sm.bmap != nullptr && total <= a.map_cap) {
-        decode_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap);
+    // Decode.  Mapped events are written in output order; larger ones use
+    // one thread per hit (bank by binary search) writing at its ranked slot.
+    if (mapped) {
+        write_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap);
         return;
     }
     for (uint32_t i = tid; i < total; i += nt) {
