@@ -16,16 +16,19 @@
 namespace utc {
 
 struct BatchedLayout {
-    size_t off_bytes, stage_byte0, sx_byte0, heads_byte0, total;
+    size_t off_bytes, stage_byte0, sx_byte0, heads_byte0, queues_byte0, fit_byte0, total;
 };
 
-__host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_words, uint32_t x_cap, int gpb) {
+__host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_words, uint32_t x_cap, int gpb,
+                                                       int warps) {
     BatchedLayout L;
     L.off_bytes = (size_t)kBigWarps * kKeyBins * 4;
     L.stage_byte0 = L.off_bytes + (((size_t)(B + 1) * 4 + 15) & ~(size_t)15);
     L.sx_byte0 = L.stage_byte0 + (size_t)stage_words * 4 + 16;
     L.heads_byte0 = L.sx_byte0 + (((size_t)x_cap * 4 + 15) & ~(size_t)15);
-    L.total = L.heads_byte0 + (size_t)gpb * sizeof(GroupHead);
+    L.queues_byte0 = L.heads_byte0 + (size_t)gpb * sizeof(GroupHead);
+    L.fit_byte0 = L.queues_byte0 + (size_t)warps * sizeof(PairQueue);
+    L.total = L.fit_byte0 + sizeof(FitTable);
     return L;
 }
 
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
     const int gl = tid % G;
     const int lane = tid & 31;
     const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, gpb);
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, gpb, NT / 32);
     DecodeSmem sm;
     sm.bigcnt = reinterpret_cast<uint32_t*>(smem);
     sm.off = reinterpret_cast<uint32_t*>(smem + L.off_bytes);
@@ -58,6 +61,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
     sm.srcmap = nullptr;
     float* sx = reinterpret_cast<float*>(smem + L.sx_byte0);
     GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.heads_byte0);
+    PairQueue* Q = reinterpret_cast<PairQueue*>(smem + L.queues_byte0) + tid / 32;
+    FitTable* ft = reinterpret_cast<FitTable*>(smem + L.fit_byte0);
+    stage_fit_table(A, ft);  // read after the loop's first barrier
 
     if (tid == 0) {
         mbar_init(&mbar, 1);
@@ -78,8 +84,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
         if (base + total > (unsigned long long)D.capacity) continue;  // reported by decode_event
         const float* X = total <= A.x_cap ? sx : D.x + base;
         const uint32_t t0 = A.trk_off[e], t1 = A.trk_off[e + 1];
-        for (uint32_t t = t0 + g; t < t1; t += gpb)
-            compass_track<G>(A, heads + g, X, sm.off, (uint32_t)base, e, t, gl, gmask);
+        const int gw = g - (lane / G);  // first group of this warp (warp-uniform loop)
+        for (uint32_t tw = t0 + gw; tw < t1; tw += gpb) {
+            const uint32_t t = tw + (uint32_t)(g - gw);
+            compass_warp<G>(A, heads + gw, ft, Q, X, sm.off, (uint32_t)base, e, t, t < t1, gl, gmask);
+        }
     }
     drain_stage(sm, phase, tma_ok);
 }
@@ -87,7 +96,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
 template <int G, int NT>
 static int launch_batched(const DecodeArgs& D, const FindArgs& A, int num_sms, cudaStream_t st) {
     const int B = 4 * D.S;
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, NT / G);
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, NT / G, NT / 32);
     const size_t smem = L.total;
     auto kern = ut_batched_kernel<G, NT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

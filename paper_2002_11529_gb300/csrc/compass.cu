@@ -26,7 +26,11 @@ __global__ void __launch_bounds__(256, 3) compass_event_kernel(const FindArgs A)
     uint32_t* soff = reinterpret_cast<uint32_t*>(smem_raw);
     const size_t off_bytes = ((size_t)(B + 1) * 4 + 15) & ~(size_t)15;
     GroupHead* heads = reinterpret_cast<GroupHead*>(smem_raw + off_bytes);
-    float* sx = reinterpret_cast<float*>(smem_raw + off_bytes + (size_t)gpb * sizeof(GroupHead));
+    PairQueue* queues = reinterpret_cast<PairQueue*>(heads + gpb);
+    FitTable* ft = reinterpret_cast<FitTable*>(queues + nt / 32);
+    float* sx = reinterpret_cast<float*>(ft + 1);
+    PairQueue* Q = queues + threadIdx.x / 32;
+    stage_fit_table(A, ft);
     const long long units = (long long)A.n_events * A.split;
     for (long long v = blockIdx.x; v < units; v += gridDim.x) {
         const int e = (int)(v / A.split), part = (int)(v % A.split);
@@ -41,8 +45,12 @@ __global__ void __launch_bounds__(256, 3) compass_event_kernel(const FindArgs A)
         const float* X = staged ? sx : A.hx + hb;
         const uint32_t t0 = A.trk_off[e], t1 = A.trk_off[e + 1];
         const uint32_t step = (uint32_t)A.split * gpb;
-        for (uint32_t t = t0 + (uint32_t)part * gpb + g; t < t1; t += step)
-            compass_track<G>(A, heads + g, X, soff, hb, e, t, gl, gmask);
+        // warp-uniform loop: the warp's first group has track tw
+        const int gw = g - (lane / G);  // first group of this warp
+        for (uint32_t tw = t0 + (uint32_t)part * gpb + gw; tw < t1; tw += step) {
+            const uint32_t t = tw + (uint32_t)(g - gw);
+            compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t, t < t1, gl, gmask);
+        }
     }
 }
 
@@ -50,6 +58,9 @@ __global__ void __launch_bounds__(256, 3) compass_event_kernel(const FindArgs A)
 // compass_fit: one thread per track.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) compass_fit_kernel(const FindArgs A) {
+    __shared__ FitTable ft;
+    stage_fit_table(A, &ft);
+    __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n_tracks) return;
     const float vx = A.vx[t], vy = A.vy[t], vtx = A.vtx[t], vty = A.vty[t];
@@ -68,7 +79,7 @@ __global__ void __launch_bounds__(256) compass_fit_kernel(const FindArgs A) {
     }
     float qop = 0.f, chi2 = 0.f, xo = vx, txo = vtx;
     float fa, fb, fq, c2;
-    if (n >= 3 && fit32(d, present, A, fa, fb, fq, c2)) {
+    if (n >= 3 && fit32(d, present, A, &ft, fa, fb, fq, c2)) {
         qop = fq;
         chi2 = c2;
         xo = vx + fa;
@@ -103,6 +114,8 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
     }
     A.x_min = g.x_min;
     A.pitch = g.sector_pitch;
+    A.inv_pitch = 1.0f / g.sector_pitch;
+    A.x_max = (double)g.x_min + (double)g.n_sectors * (double)g.sector_pitch;
     A.z_velo = g.z_velo;
     A.n_sec = p->n_sectors;
     A.n_cand = p->n_candidates;
@@ -199,7 +212,8 @@ static int launch_find(FindArgs A, int block, int num_sms, cudaStream_t st) {
     A.split = (int)fmax(1.0, fmin(64.0, tpe / (2.0 * gpb)));
     A.x_cap = 8192;
     const size_t off_bytes = ((size_t)(B + 1) * 4 + 15) & ~(size_t)15;
-    const size_t smem = off_bytes + (size_t)gpb * sizeof(GroupHead) + (size_t)A.x_cap * sizeof(float);
+    const size_t smem = off_bytes + (size_t)gpb * sizeof(GroupHead) + (size_t)(block / 32) * sizeof(PairQueue) +
+                        sizeof(FitTable) + (size_t)A.x_cap * sizeof(float);
     if (cudaFuncSetAttribute(compass_event_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return UT_ERR_CUDA;

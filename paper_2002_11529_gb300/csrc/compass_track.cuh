@@ -47,6 +47,8 @@ struct FindArgs {
     int S;
     float z[4], tan_a[4];
     float x_min, pitch, z_velo;
+    float inv_pitch;             // 1 / pitch (float estimate of the sector)
+    double x_max;                // x_min + S * pitch in double
     int n_sec, n_cand;
     float slope_tol, tol_kink, tol_col, chi2ndof_max, z_kink;
     float hw[4], t[4], f[4];
@@ -89,10 +91,30 @@ __device__ __forceinline__ LayerPred predict(const FindArgs& a, float vx, float 
     p.u = xv - yv * (double)a.tan_a[l];
     p.hi = (float)p.u;
     p.lo = (float)(p.u - (double)p.hi);
-    const double q = (p.u - (double)a.x_min) / (double)a.pitch;
-    const double fq = fmin(fmax(floor(q), 0.0), (double)(a.S - 1));
-    p.c = (int)fq;
+    // central sector floor((u - x_min) / pitch) in double, clamped; a float
+    // estimate decides whenever it is farther than 1e-3 + 1e-5 |q| from an
+    // integer, far above its error (a few 1e-7 of |q| + |x_min| / pitch)
+    const float qf = __fmul_rn(__fsub_rn(p.hi, a.x_min), a.inv_pitch);
+    if (fabsf(__fsub_rn(qf, rintf(qf))) >= __fadd_rn(1e-3f, __fmul_rn(1e-5f, fabsf(qf)))) {
+        p.c = (int)fminf(fmaxf(floorf(qf), 0.f), (float)(a.S - 1));
+    } else {
+        const double q = (p.u - (double)a.x_min) / (double)a.pitch;
+        const double fq = fmin(fmax(floor(q), 0.0), (double)(a.S - 1));
+        p.c = (int)fq;
+    }
     return p;
+}
+
+// The fit factors of FindArgs staged in shared memory (looked up with a
+// lane-dependent presence mask).
+struct FitTable {
+    float fac[16][6];
+    int ok[16];
+};
+
+__device__ __forceinline__ void stage_fit_table(const FindArgs& A, FitTable* ft) {
+    for (int i = threadIdx.x; i < 16 * 6; i += blockDim.x) ft->fac[i / 6][i % 6] = A.fac[i / 6][i % 6];
+    for (int i = threadIdx.x; i < 16; i += blockDim.x) ft->ok[i] = A.fac_ok[i];
 }
 
 // Closed-form p-kick fit in float (Sec. III-C): residual model
@@ -104,8 +126,8 @@ __device__ __forceinline__ LayerPred predict(const FindArgs& a, float vx, float 
 // those factors depend only on the presence mask and come from a table
 // (fit_factors, computed with exactly these operations).  Per candidate:
 // right-hand side, forward / diagonal / back substitution, chi2.
-__device__ __forceinline__ bool fit32(const float* d, const bool* present, const FindArgs& A, float& a_o,
-                                      float& b_o, float& q_o, float& chi2_o) {
+__device__ __forceinline__ bool fit32(const float* d, const bool* present, const FindArgs& A, const FitTable* ft,
+                                      float& a_o, float& b_o, float& q_o, float& chi2_o) {
     const float w = A.w;
     int mask = 0;
     float Bd = 0.f, Btd = 0.f, Bfd = 0.f;
@@ -117,9 +139,9 @@ __device__ __forceinline__ bool fit32(const float* d, const bool* present, const
         Btd = Btd + A.wt[l] * d[l];
         Bfd = Bfd + A.wf[l] * d[l];
     }
-    if (!A.fac_ok[mask]) return false;
-    const float D1 = A.fac[mask][0], D2 = A.fac[mask][1], D3 = A.fac[mask][2];
-    const float L21 = A.fac[mask][3], L31 = A.fac[mask][4], L32 = A.fac[mask][5];
+    if (!ft->ok[mask]) return false;
+    const float D1 = ft->fac[mask][0], D2 = ft->fac[mask][1], D3 = ft->fac[mask][2];
+    const float L21 = ft->fac[mask][3], L31 = ft->fac[mask][4], L32 = ft->fac[mask][5];
     const float y1 = Bd;
     const float y2 = Btd - L21 * y1;
     const float y3 = Bfd - L31 * y1 - L32 * y2;
@@ -142,8 +164,13 @@ __device__ __forceinline__ bool fit32(const float* d, const bool* present, const
     return true;
 }
 
+// Valid tracklets of one track and direction kept by the warp search.
+constexpr int kListCap = 32;
+
 // Per-track (lane group) shared state; positions are event-local.
 struct GroupHead {
+    unsigned long long best;     // packed key of the best valid tracklet (warp search)
+    unsigned long long list[kListCap];  // packed keys of the first kListCap valid tracklets found
     int wfirst[4][kMaxSectors];  // first hit of each slot window
     int wsize[4][kMaxSectors];
     int pre[4][kMaxSectors];     // combined-range index of the window's first hit
@@ -151,10 +178,26 @@ struct GroupHead {
     int sec0[4];                 // first searched sector
     int cen[4];                  // central sector
     float scale[4];              // union positions per mm (start of lower-bound walks)
+    float hi[4], lo[4];          // prediction per layer (float pair)
+    int act;                     // track takes part in the current warp search
+    int count;                   // valid tracklets found by the warp search
+    int ovf;                     // a combined index did not fit the packed key
+    int rpos[4];                 // record of the best tracklet of the warp search
+    float ra, rb, rq, rc2;
+    int rnh;
+};
+
+// Pairs (first anchor, second anchor) of a warp waiting for evaluation.
+constexpr int kPairQ = 64;
+struct PairQueue {
+    int pa[kPairQ];
+    int pb[kPairQ];
+    int u[kPairQ];               // group slot of the pair's track
 };
 
 struct View {
     const GroupHead* h;
+    const FitTable* ft;
     const float* X;              // event hit x (shared or global memory)
     const uint32_t* off;         // event-local bank offsets (B + 1)
     int S;
@@ -272,7 +315,7 @@ __device__ __forceinline__ bool eval_pair(const FindArgs& A, const View& V, int 
     }
     if (nh < 3) return false;
     float fa, fb, fq, c2;
-    if (!fit32(dl, present, A, fa, fb, fq, c2)) return false;
+    if (!fit32(dl, present, A, V.ft, fa, fb, fq, c2)) return false;
     const float c2n = c2 / (float)(nh - 1);
     if (!(c2n <= A.chi2ndof_max)) return false;
     out.nh = nh;
@@ -424,7 +467,7 @@ __device__ __forceinline__ int scan_anchor(const FindArgs& A, const View& V, int
 // Ordered path of one direction (lanes take consecutive first anchors; a
 // prefix count over lanes keeps exactly the first n_candidates).
 template <int G, int DIR>
-__device__ __forceinline__ void ordered_dir(const FindArgs& A, const View& V, int na, int gl, uint32_t gmask,
+__device__ __noinline__ void ordered_dir(const FindArgs& A, const View& V, int na, int gl, uint32_t gmask,
                                             int& best_nh, float& best_c2, int& best_pa, int& best_pb) {
     int count = 0;
     for (int ia0 = 0; ia0 < na && count < A.n_cand; ia0 += G) {
@@ -477,7 +520,7 @@ __device__ __forceinline__ void ordered_dir(const FindArgs& A, const View& V, in
 }
 
 template <int G, int DIR>
-__device__ __forceinline__ void search_direction(const FindArgs& A, const View& V, int gl, uint32_t gmask,
+__device__ __noinline__ void search_direction(const FindArgs& A, const View& V, int gl, uint32_t gmask,
                                                  int& best_nh, float& best_c2, int& best_pa, int& best_pb) {
     constexpr int la = DIR ? 3 : 0;
     const int total = fast_dir<G, DIR>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
@@ -490,11 +533,20 @@ __device__ __forceinline__ void search_direction(const FindArgs& A, const View& 
     }
 }
 
-// One VELO track t of event e.  X / off: the event's hit x and bank offsets
-// (event-local); hb: global index of the event's first hit.
+// eval_pair of a selected pair outside the hot loops (kept out of line).
+template <int DIR>
+__device__ __noinline__ void eval_pair_cold(const FindArgs& A, const View& V, int pa, int pb, Tracklet& tk) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    eval_pair<DIR>(A, V, pa, pb, V.d(la, pa), V.d(lb, pb), tk);
+}
+
+// Setup of VELO track t of event e by its lane group: extrapolation
+// (Sec. V-A), default outputs, the windows and their slot parts.  Returns
+// whether the track is searched (accepted, some window not empty); V gets
+// the group's view.
 template <int G>
-__device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head, const float* X, const uint32_t* off,
-                                              uint32_t hb, int e, uint32_t t, int gl, uint32_t gmask) {
+__device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, const FitTable* ft, const float* X,
+                                            const uint32_t* off, int e, uint32_t t, int gl, uint32_t gmask, View& V) {
     const int S = A.S, n_sec = A.n_sec;
     const float vx = A.vx[t], vy = A.vy[t], vtx = A.vtx[t], vty = A.vty[t];
     const bool backward = (A.vflags[t] & 1u) != 0;
@@ -505,8 +557,8 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
     mine.c = 0;
     mine.u = 0.0;
     if (gl < 4) mine = predict(A, vx, vy, vtx, vty, gl);
-    View V;
     V.h = head;
+    V.ft = ft;
     V.X = X;
     V.off = off;
     V.S = S;
@@ -516,8 +568,7 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
         V.lo[l] = __shfl_sync(gmask, mine.lo, l, G);
     }
     const double u0 = __shfl_sync(gmask, mine.u, 0, G);
-    const double x_max = (double)A.x_min + (double)A.S * (double)A.pitch;
-    const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= x_max);
+    const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= A.x_max);
 
     if (gl == 0) {
 #pragma unroll
@@ -532,7 +583,7 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
     if (!accept) {
         if (A.win)
             for (int j = gl; j < 4 * n_sec * 2; j += G) A.win[(size_t)t * 4 * n_sec * 2 + j] = -1;
-        return;
+        return false;
     }
 
     // Windows (Sec. V-A): union of the layer's windows, then each slot's part.
@@ -559,6 +610,8 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
         head->sec0[l] = s0;
         head->cen[l] = c;
         head->scale[l] = a > w0 ? (float)(a - w0) / (2.f * hw) : 0.f;
+        head->hi[l] = uh;
+        head->lo[l] = ul;
     }
     __syncwarp(gmask);
     for (int j = gl; j < 4 * n_sec; j += G) {
@@ -599,25 +652,286 @@ __device__ __forceinline__ void compass_track(const FindArgs& A, GroupHead* head
     int any = 0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) any |= head->wunion[l][1] - head->wunion[l][0];
-    if (any == 0) return;
+    return any != 0;
+}
 
-    // Tracklet search (Sec. V-B): forward, then backward only if forward
-    // found no valid tracklet.
+// Packed order of a valid tracklet for the warp search: the smallest key
+// is the best (most hits, then lowest chi2, then earliest combined order of
+// the anchors).  chi2 >= 0, so its float bits order like the values.
+__device__ __forceinline__ unsigned long long tracklet_key(int nh, float chi2, int ca, int cb) {
+    return ((unsigned long long)(nh < 4) << 63) | ((unsigned long long)__float_as_uint(chi2) << 31) |
+           ((unsigned long long)ca << 16) | (unsigned long long)cb;
+}
+
+// Fast path of one direction for all tracks of a warp with act set
+// (Sec. V-B).  The first anchors of those tracks are taken 32 at a time
+// across the whole warp; each lane finds its anchor's band of second
+// anchors, and the (anchor, second anchor) pairs join the warp's queue
+// (lane q appends pair q of the warp-wide prefix count).  Whenever 32 pairs
+// are queued they are evaluated exactly, one per lane; each track keeps the
+// minimum packed key of its valid tracklets, their count, the keys of the
+// first kListCap of them, and a record of the tracklet holding the minimum.
+// A track whose count exceeds kListCap takes no further anchors (the
+// sequential ordered path decides it).
+template <int DIR>
+__device__ __forceinline__ void eval_queued(const FindArgs& A, GroupHead* wh, const FitTable* ft, const float* X,
+                                            const uint32_t* off, const PairQueue* Q, int k, int lane) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    bool valid = false;
+    unsigned long long key = 0;
+    Tracklet tk;
+    GroupHead* h = wh;
+    if (lane < k) {
+        h = wh + Q->u[lane];
+        View V;
+        V.h = h;
+        V.ft = ft;
+        V.X = X;
+        V.off = off;
+        V.S = A.S;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            V.hi[l] = h->hi[l];
+            V.lo[l] = h->lo[l];
+        }
+        const int pa = Q->pa[lane], pb = Q->pb[lane];
+        if (eval_pair<DIR>(A, V, pa, pb, V.d(la, pa), V.d(lb, pb), tk)) {
+            const int ca = V.comb(la, pa), cb = V.comb(lb, pb);
+            if (ca >= 32768 || cb >= 65536) atomicOr(&h->ovf, 1);
+            key = tracklet_key(tk.nh, tk.chi2, ca & 0x7FFF, cb & 0xFFFF);
+            atomicMin(&h->best, key);
+            const int idx = atomicAdd(&h->count, 1);
+            if (idx < kListCap) h->list[idx] = key;
+            valid = true;
+        }
+    }
+    __syncwarp();
+    if (valid && h->best == key) {  // keys are unique: one writer per track
+#pragma unroll
+        for (int l = 0; l < 4; ++l) h->rpos[l] = tk.pos[l];
+        h->ra = tk.a;
+        h->rb = tk.b;
+        h->rq = tk.q;
+        h->rc2 = tk.chi2;
+        h->rnh = tk.nh;
+    }
+    __syncwarp();
+}
+
+// Moves queue entries [32, 32 + rest) to the front (rest < 32).
+__device__ __forceinline__ void queue_shift(PairQueue* Q, int rest, int lane) {
+    int r_pa = 0, r_pb = 0, r_u = 0;
+    if (lane < rest) {
+        r_pa = Q->pa[32 + lane];
+        r_pb = Q->pb[32 + lane];
+        r_u = Q->u[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        Q->pa[lane] = r_pa;
+        Q->pb[lane] = r_pb;
+        Q->u[lane] = r_u;
+    }
+    __syncwarp();
+}
+
+template <int T, int DIR>
+__device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft, PairQueue* Q, const float* X,
+                            const uint32_t* off, int lane) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const int na = lane < T && wh[lane].act ? wh[lane].wunion[la][1] - wh[lane].wunion[la][0] : 0;
+    int pre = na;
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    int pre_s[T];  // inclusive anchor prefix per slot
+#pragma unroll
+    for (int u = 0; u < T; ++u) pre_s[u] = __shfl_sync(0xffffffffu, pre, u);
+    const int n_anchor = pre_s[T - 1];
+    int nq = 0;  // queued pairs (warp-uniform)
+    for (int ab = 0; ab < n_anchor; ab += 32) {
+        const int ia = ab + lane;
+        int u = 0;
+#pragma unroll
+        for (int s = 0; s < T; ++s) u += pre_s[s] <= ia;
+        int c = 0, p0 = 0, pa = 0;
+        if (ia < n_anchor && wh[u].count <= kListCap) {
+            const GroupHead* h = wh + u;
+            View V;
+            V.h = h;
+            V.X = X;
+            V.off = off;
+            V.S = A.S;
+            V.hi[la] = h->hi[la];
+            V.lo[la] = h->lo[la];
+            V.hi[lb] = h->hi[lb];
+            V.lo[lb] = h->lo[lb];
+            int excl = 0;
+#pragma unroll
+            for (int s = 0; s < T; ++s)
+                if (s == u - 1) excl = pre_s[s];
+            pa = h->wunion[la][0] + (ia - excl);
+            const float da = V.d(la, pa);
+            float blo, bhi;
+            kink_band<DIR>(A, da, blo, bhi);
+            const int wb1 = h->wunion[lb][1];
+            p0 = V.lower(lb, blo, A.hw[lb]);
+            int p1 = p0;
+            while (p1 < wb1 && V.d(lb, p1) <= bhi) ++p1;
+            c = p1 - p0;
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int n_pair = __shfl_sync(0xffffffffu, incl, 31);
+        for (int q0 = 0; q0 < n_pair; q0 += 32) {
+            const int q = q0 + lane;
+            // owner lane j of pair q: first lane with incl > q
+            int j = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, j + st - 1);
+                if (v <= q) j += st;
+            }
+            j = min(j, 31);
+            const int j_u = __shfl_sync(0xffffffffu, u, j);
+            const int j_pa = __shfl_sync(0xffffffffu, pa, j);
+            const int j_p0 = __shfl_sync(0xffffffffu, p0, j);
+            const int j_ex = __shfl_sync(0xffffffffu, incl - c, j);
+            const int m = min(32, n_pair - q0);
+            if (lane < m) {
+                Q->pa[nq + lane] = j_pa;
+                Q->pb[nq + lane] = j_p0 + (q - j_ex);
+                Q->u[nq + lane] = j_u;
+            }
+            nq += m;
+            __syncwarp();
+            if (nq >= 32) {
+                eval_queued<DIR>(A, wh, ft, X, off, Q, 32, lane);
+                nq -= 32;
+                queue_shift(Q, nq, lane);
+            }
+        }
+    }
+    if (nq > 0) eval_queued<DIR>(A, wh, ft, X, off, Q, nq, lane);
+}
+
+// Outcome of the warp search of direction DIR for the group's track (group
+// code).  At most n_candidates valid: the best by the packed key, from the
+// record.  More: the sequential order keeps the first n_candidates valid
+// tracklets, and that order is the (first anchor, second anchor) combined
+// order held in the low 31 bits of the key; so with all of them listed the
+// answer is the minimum key among the n_candidates smallest order keys.
+// More than kListCap valid: the sequential ordered path.  A combined index
+// that overflowed the key: the per-group fast path.
+template <int G, int DIR>
+__device__ __forceinline__ void resolve_direction(const FindArgs& A, const View& V, int gl, uint32_t gmask,
+                                                  int& best_nh, float& best_c2, int& best_pa, int& best_pb,
+                                                  bool& from_record) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const GroupHead* h = V.h;
+    const int count = h->count;
+    best_nh = 0;
+    best_c2 = 0.f;
+    best_pa = best_pb = -1;
+    from_record = false;
+    if (count == 0) return;
+    if (h->ovf) {
+        search_direction<G, DIR>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    } else if (count > kListCap) {
+        const int na = h->wunion[la][1] - h->wunion[la][0];
+        ordered_dir<G, DIR>(A, V, na, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    } else if (count > A.n_cand) {
+        unsigned long long best = ~0ull;
+        for (int i = gl; i < count; i += G) {
+            const unsigned long long ki = h->list[i];
+            const uint32_t oi = (uint32_t)(ki & 0x7FFFFFFFull);
+            int r = 0;
+            for (int j = 0; j < count; ++j) r += (uint32_t)(h->list[j] & 0x7FFFFFFFull) < oi;
+            if (r < A.n_cand && ki < best) best = ki;
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(gmask, best, o, G);
+            best = ob < best ? ob : best;
+        }
+        best_nh = (best >> 63) ? 3 : 4;
+        best_c2 = __uint_as_float((uint32_t)(best >> 31));
+        best_pa = slot_pos(h, la, A.n_sec, (int)((best >> 16) & 0x7FFFu));
+        best_pb = slot_pos(h, lb, A.n_sec, (int)(best & 0xFFFFu));
+    } else {
+        best_nh = h->rnh;
+        best_c2 = h->rc2;
+        best_pa = h->rpos[la];
+        best_pb = h->rpos[lb];
+        from_record = true;
+    }
+}
+
+// The VELO tracks of one warp: group u of G lanes has track t (has_track),
+// with its GroupHead at wh[u].  Setup per group, forward warp search,
+// resolution per group, backward warp search for the tracks without a
+// forward tracklet, then the selected tracklet is evaluated again for its
+// hits and fit and written.  Every lane of the warp calls this together.
+template <int G>
+__device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* ft, PairQueue* Q, const float* X,
+                             const uint32_t* off, uint32_t hb, int e, uint32_t t, bool has_track, int gl,
+                             uint32_t gmask) {
+    constexpr int T = 32 / G;
+    const int lane = threadIdx.x & 31;
+    GroupHead* head = wh + lane / G;
+    View V;
+    const bool active = has_track && setup_track<G>(A, head, ft, X, off, e, t, gl, gmask, V);
+    if (gl == 0) {
+        head->act = active;
+        head->best = ~0ull;
+        head->count = 0;
+        head->ovf = 0;
+    }
+    __syncwarp();
+    warp_search<T, 0>(A, wh, ft, Q, X, off, lane);
     int best_nh = 0, best_dir = 0, best_pa = -1, best_pb = -1;
     float best_c2 = 0.f;
-    search_direction<G, 0>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
-    if (best_nh == 0) {
-        best_dir = 1;
-        search_direction<G, 1>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb);
+    bool rec = false;
+    if (active) resolve_direction<G, 0>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb, rec);
+    __syncwarp();
+    if (gl == 0) {
+        head->act = active && best_nh == 0;
+        head->best = ~0ull;
+        head->count = 0;
+        head->ovf = 0;
     }
-    if (best_nh == 0 || gl != 0) return;
+    __syncwarp();
+    warp_search<T, 1>(A, wh, ft, Q, X, off, lane);
+    if (active && best_nh == 0) {
+        best_dir = 1;
+        resolve_direction<G, 1>(A, V, gl, gmask, best_nh, best_c2, best_pa, best_pb, rec);
+    }
+    __syncwarp();
+    if (!active || best_nh == 0 || gl != 0) return;
 
-    // Re-evaluate the selected tracklet for its hits and fit.
+    // The selected tracklet: from the warp search's record, else evaluated
+    // again for its hits and fit.
+    const float vx = A.vx[t], vtx = A.vtx[t];
     Tracklet tk;
-    if (best_dir == 0)
-        eval_pair<0>(A, V, best_pa, best_pb, V.d(0, best_pa), V.d(2, best_pb), tk);
-    else
-        eval_pair<1>(A, V, best_pa, best_pb, V.d(3, best_pa), V.d(1, best_pb), tk);
+    if (rec) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) tk.pos[l] = head->rpos[l];
+        tk.nh = head->rnh;
+        tk.chi2 = head->rc2;
+        tk.a = head->ra;
+        tk.b = head->rb;
+        tk.q = head->rq;
+    } else if (best_dir == 0) {
+        eval_pair_cold<0>(A, V, best_pa, best_pb, tk);
+    } else {
+        eval_pair_cold<1>(A, V, best_pa, best_pb, tk);
+    }
 #pragma unroll
     for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.pos[l] >= 0 ? (int)(hb + tk.pos[l]) : -1;
     A.qop[t] = tk.q;

@@ -324,32 +324,33 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
         }
     }
     __syncthreads();
-    if (!SORT) return;
-    for (uint32_t i = tid; i < total; i += nt) {
-        const int b = bmap[i];
-        const uint32_t o0 = off[b], n = off[b + 1] - o0;
-        if (n > (uint32_t)kSmallBank) continue;
-        const uint32_t key = srcm[i];
-        const uint16_t* K = srcm + o0;
-        uint32_t r = 0, j = 0;
-        for (; j + 4 <= n; j += 4)
-            r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
-                 (uint32_t)(K[j + 3] < key);
-        for (; j < n; ++j) r += (uint32_t)(K[j] < key);
-        bmap[i] = (uint16_t)(b | (r << 10));
+    if constexpr (SORT) {
+        for (uint32_t i = tid; i < total; i += nt) {
+            const int b = bmap[i];
+            const uint32_t o0 = off[b], n = off[b + 1] - o0;
+            if (n > (uint32_t)kSmallBank) continue;
+            const uint32_t key = srcm[i];
+            const uint16_t* K = srcm + o0;
+            uint32_t r = 0, j = 0;
+            for (; j + 4 <= n; j += 4)
+                r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
+                     (uint32_t)(K[j + 3] < key);
+            for (; j < n; ++j) r += (uint32_t)(K[j] < key);
+            bmap[i] = (uint16_t)(b | (r << 10));
+        }
+        rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
+            srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
+        });
+        __syncthreads();
+        for (uint32_t i = tid; i < total; i += nt) {
+            const uint32_t v = bmap[i];
+            const int b = (int)(v & 0x3FFu);
+            const uint32_t o0 = off[b];
+            if (off[b + 1] - o0 > (uint32_t)kSmallBank) continue;
+            srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
+        }
+        __syncthreads();
     }
-    rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
-        srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
-    });
-    __syncthreads();
-    for (uint32_t i = tid; i < total; i += nt) {
-        const uint32_t v = bmap[i];
-        const int b = (int)(v & 0x3FFu);
-        const uint32_t o0 = off[b];
-        if (off[b + 1] - o0 > (uint32_t)kSmallBank) continue;
-        srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
-    }
-    __syncthreads();
 }
 
 // Writes of a mapped event in output order; groups of four outputs that
