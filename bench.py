@@ -17,6 +17,7 @@ method) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import statistics
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
+    ap.add_argument("--events", type=int, default=None,
+                    help="first N events of the workload's generator (smaller cases for profiling)")
     ap.add_argument("--form", default="fused", choices=["batched", "fused", "plain"])
     ap.add_argument("--autotune", action="store_true", help="pick the batched launch shape by a sweep")
     ap.add_argument("--x-cap", type=int, default=8192)
@@ -54,17 +57,19 @@ def parse():
     return ap.parse_args()
 
 
-def make_batch(wl, rank):
+def make_batch(wl, rank, n_events=None):
     import synth
     c = dict(WORKLOADS[wl])
     c.pop("name")
+    if n_events is not None:
+        c["n_events"] = n_events
     c["seed"] = c["seed"] + 1000 * rank
     return synth.generate(**c)
 
 
 def workload_config(wl, batch, form, extra=None):
     c = WORKLOADS[wl]
-    cfg = {"workload": f"{wl}: {c['n_events']} events, 4x{c['n_sectors']} sectors, "
+    cfg = {"workload": f"{wl}: {batch.n_events} events, 4x{c['n_sectors']} sectors, "
                        f"hits/event {c['hits']}, tracks/event {c['tracks'] or '0.05*hits'}",
            "n_events": batch.n_events, "hits_per_event": round(batch.n_hits / batch.n_events, 1),
            "tracks_per_event": round(batch.n_tracks / batch.n_events, 1),
@@ -128,6 +133,33 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def source_digest():
+    """sha256 over the CUDA sources and the ABI header (sorted by name)."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2002_11529_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for path in files:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+    recorded in profiles/traffic.json for this kernel and workload, or None
+    when absent or taken on other sources than the current ones."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(f"{kernel}|{workload}")
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256") != source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(batch, params, min_seconds=10.0):
@@ -287,7 +319,7 @@ def main():
         dist.init_process_group("nccl")
     g.build.build()
 
-    batch = make_batch(args.workload, rank)
+    batch = make_batch(args.workload, rank, args.events)
     params = synth.CompassParams()
     ctx = g.Context(batch.geom)
     pipe = g.Pipeline(ctx, batch, params)
@@ -429,7 +461,7 @@ def main():
                        "frac": round(gbs / hbm, 4), "share": round(ms / (tot_ms / args.steps), 3)}
     dom = max(kern, key=lambda n: kinfo[n]["ms"])
     roof = {"kernel": dom, "bound": "hbm", "achieved": kinfo[dom]["achieved_gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": kinfo[dom]["frac"], "traffic": None,
+            "unit": "GB/s", "frac": kinfo[dom]["frac"], "traffic": measured_traffic(dom, args.workload),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
     lat = sorted(step_ms)
     p = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]

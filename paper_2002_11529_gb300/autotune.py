@@ -1,9 +1,10 @@
 """Autotuner for the batched form's launch shape.
 
-Sweeps tracks per warp {1, 2, 4, 8} and block size {256, 512} (the
-per-event shared-memory tile stays at 8192 hits) on the caller's batch (device
-resident), times each with CUDA events over several passes (L2 flushed
-before each pass), and returns the fastest LaunchConfig with the table.
+Sweeps tracks per warp {1, 2, 4, 8} and block size {128, 256, 512} (the
+per-event shared-memory tile of hit x stays at 8192 hits) on the caller's
+batch (device resident), times each with CUDA events over several passes
+(L2 flushed before each pass), and returns the fastest LaunchConfig with
+the table.
 Results can be cached in a JSON file keyed by the batch's shape.
 """
 from __future__ import annotations
@@ -18,7 +19,7 @@ import torch
 from . import LaunchConfig
 
 TRACKS_PER_WARP = (1, 2, 4, 8)
-BLOCKS = (256, 512)
+BLOCKS = (128, 256, 512)
 X_CAPS = (8192,)
 
 

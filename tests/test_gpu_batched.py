@@ -113,7 +113,9 @@ def test_autotuner_picks_a_valid_config(g):
     ctx = g.Context(b.geom)
     pipe = g.Pipeline(ctx, b, P)
     best, table = autotune.autotune(pipe, reps=1)
-    assert len(table) == 8 and all(ms > 0 for _, ms in table)
+    n_shapes = len(autotune.TRACKS_PER_WARP) * len(autotune.BLOCKS) * len(autotune.X_CAPS)
+    assert len(table) == n_shapes and all(ms > 0 for _, ms in table)
+    assert {c.block for c, _ in table} == {128, 256, 512} and best in [c for c, _ in table]
     pipe.run_batched(best)
     ctx.check(what="autotuned")
     check_against_oracle(g, pipe, b)
