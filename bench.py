@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--form", default="fused", choices=["batched", "fused", "plain"])
     ap.add_argument("--autotune", action="store_true", help="pick the batched launch shape by a sweep")
     ap.add_argument("--x-cap", type=int, default=8192)
-    ap.add_argument("--tracks-per-warp", type=int, default=4)
+    ap.add_argument("--tracks-per-warp", type=int, default=8)
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",

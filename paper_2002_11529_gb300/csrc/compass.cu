@@ -14,7 +14,7 @@
 namespace utc {
 
 template <int G>
-__global__ void __launch_bounds__(256, 3) compass_event_kernel(const FindArgs A) {
+__global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int S = A.S, B = 4 * S;
     const int nt = blockDim.x;

@@ -587,31 +587,46 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
     }
 
     // Windows (Sec. V-A): union of the layer's windows, then each slot's part.
-    // (lane l uses its own prediction: no runtime index into V.hi / V.lo,
-    // which would move them to local memory)
-    if (gl < 4) {
-        const int l = gl, c = mine.c;
-        const float hw = A.hw[l], uh = mine.hi, ul = mine.lo;
+    // Lane l (< 4) takes layer l; with G >= 8, lane l + 4 finds the upper end
+    // of the same window while lane l finds the lower end.  (Each lane uses
+    // its own copy of the prediction: no runtime index into V.hi / V.lo,
+    // which would move them to local memory.)
+    {
+        const int l = gl & 3;
+        const float uh = __shfl_sync(gmask, mine.hi, l, G), ul = __shfl_sync(gmask, mine.lo, l, G);
+        const int c = __shfl_sync(gmask, mine.c, l, G);
         const int s0 = max(c - n_sec / 2, 0), s1 = min(c + (n_sec - 1) / 2, S - 1);
-        const int ra = (int)off[l * S + s0], rb = (int)off[l * S + s1 + 1];
-        int a = ra, b = rb;
-        while (a < b) {
-            const int m = (a + b) >> 1;
-            if ((X[m] - uh) - ul >= -hw) b = m; else a = m + 1;
+        int w0 = 0, w1 = 0;
+        if (gl < (G >= 8 ? 8 : 4)) {
+            const float hw = A.hw[l];
+            const int ra = (int)off[l * S + s0], rb = (int)off[l * S + s1 + 1];
+            int a = ra, b = rb;
+            if (G < 8 || gl < 4) {
+                while (a < b) {
+                    const int m = (a + b) >> 1;
+                    if ((X[m] - uh) - ul >= -hw) b = m; else a = m + 1;
+                }
+                w0 = a;
+                b = rb;
+            }
+            if (G < 8 || gl >= 4) {
+                while (a < b) {
+                    const int m = (a + b) >> 1;
+                    if ((X[m] - uh) - ul > hw) b = m; else a = m + 1;
+                }
+                w1 = a;
+            }
         }
-        const int w0 = a;
-        b = rb;
-        while (a < b) {
-            const int m = (a + b) >> 1;
-            if ((X[m] - uh) - ul > hw) b = m; else a = m + 1;
+        if constexpr (G >= 8) w1 = __shfl_sync(gmask, w1, l + 4, G);
+        if (gl < 4) {
+            head->wunion[l][0] = w0;
+            head->wunion[l][1] = w1;
+            head->sec0[l] = s0;
+            head->cen[l] = c;
+            head->scale[l] = w1 > w0 ? (float)(w1 - w0) / (2.f * A.hw[l]) : 0.f;
+            head->hi[l] = uh;
+            head->lo[l] = ul;
         }
-        head->wunion[l][0] = w0;
-        head->wunion[l][1] = a;
-        head->sec0[l] = s0;
-        head->cen[l] = c;
-        head->scale[l] = a > w0 ? (float)(a - w0) / (2.f * hw) : 0.f;
-        head->hi[l] = uh;
-        head->lo[l] = ul;
     }
     __syncwarp(gmask);
     for (int j = gl; j < 4 * n_sec; j += G) {
