@@ -626,41 +626,36 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
             head->scale[l] = w1 > w0 ? (float)(w1 - w0) / (2.f * A.hw[l]) : 0.f;
             head->hi[l] = uh;
             head->lo[l] = ul;
-        }
-    }
-    __syncwarp(gmask);
-    for (int j = gl; j < 4 * n_sec; j += G) {
-        const int l = j / n_sec, k = j % n_sec;
-        const int s = head->cen[l] + ((k + 1) >> 1) * ((k & 1) ? -1 : 1);
-        int first = 0, size = 0;
-        if (s >= 0 && s < S) {
-            first = max((int)off[l * S + s], head->wunion[l][0]);
-            size = max(0, min((int)off[l * S + s + 1], head->wunion[l][1]) - first);
-        }
-        head->wfirst[l][k] = first;
-        head->wsize[l][k] = size;
-        if (A.win) {
-            int16_t* wp = A.win + (((size_t)t * 4 + l) * n_sec + k) * 2;
-            int16_t v0 = -1, v1 = -1;
-            if (size > 0) {
-                const long long rel = (long long)first - (long long)off[l * S];
-                if (rel > 32767 || size > 32767) {
-                    report(A.status, UT_ERR_WIN16, e, (long long)(t - A.trk_off[e]));
-                } else {
-                    v0 = (int16_t)rel;
-                    v1 = (int16_t)size;
+            // the slot windows of layer l in slot order c, c-1, c+1, c-2, c+2
+            // (each sector's part of the union) and their combined-range starts
+            int pre = 0;
+            for (int k = 0; k < n_sec; ++k) {
+                const int sk = c + ((k + 1) >> 1) * ((k & 1) ? -1 : 1);
+                int first = 0, size = 0;
+                if (sk >= 0 && sk < S) {
+                    first = max((int)off[l * S + sk], w0);
+                    size = max(0, min((int)off[l * S + sk + 1], w1) - first);
+                }
+                head->wfirst[l][k] = first;
+                head->wsize[l][k] = size;
+                head->pre[l][k] = pre;
+                pre += size;
+                if (A.win) {
+                    int16_t* wp = A.win + (((size_t)t * 4 + l) * n_sec + k) * 2;
+                    int16_t v0 = -1, v1 = -1;
+                    if (size > 0) {
+                        const long long rel = (long long)first - (long long)off[l * S];
+                        if (rel > 32767 || size > 32767) {
+                            report(A.status, UT_ERR_WIN16, e, (long long)(t - A.trk_off[e]));
+                        } else {
+                            v0 = (int16_t)rel;
+                            v1 = (int16_t)size;
+                        }
+                    }
+                    wp[0] = v0;
+                    wp[1] = v1;
                 }
             }
-            wp[0] = v0;
-            wp[1] = v1;
-        }
-    }
-    __syncwarp(gmask);
-    if (gl < 4) {
-        int pre = 0;
-        for (int k = 0; k < n_sec; ++k) {
-            head->pre[gl][k] = pre;
-            pre += head->wsize[gl][k];
         }
     }
     __syncwarp(gmask);
@@ -761,16 +756,15 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
         const int v = __shfl_up_sync(0xffffffffu, pre, o);
         if (lane >= o) pre += v;
     }
-    int pre_s[T];  // inclusive anchor prefix per slot
-#pragma unroll
-    for (int u = 0; u < T; ++u) pre_s[u] = __shfl_sync(0xffffffffu, pre, u);
-    const int n_anchor = pre_s[T - 1];
+    // lane s < T holds the inclusive anchor prefix of slot s
+    const int n_anchor = __shfl_sync(0xffffffffu, pre, T - 1);
     int nq = 0;  // queued pairs (warp-uniform)
     for (int ab = 0; ab < n_anchor; ab += 32) {
         const int ia = ab + lane;
         int u = 0;
 #pragma unroll
-        for (int s = 0; s < T; ++s) u += pre_s[s] <= ia;
+        for (int s = 0; s < T; ++s) u += __shfl_sync(0xffffffffu, pre, s) <= ia;
+        const int excl = __shfl_sync(0xffffffffu, pre, max(u - 1, 0)) * (u > 0);
         int c = 0, p0 = 0, pa = 0;
         if (ia < n_anchor && wh[u].count <= kListCap) {
             const GroupHead* h = wh + u;
@@ -783,10 +777,6 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             V.lo[la] = h->lo[la];
             V.hi[lb] = h->hi[lb];
             V.lo[lb] = h->lo[lb];
-            int excl = 0;
-#pragma unroll
-            for (int s = 0; s < T; ++s)
-                if (s == u - 1) excl = pre_s[s];
             pa = h->wunion[la][0] + (ia - excl);
             const float da = V.d(la, pa);
             float blo, bhi;
@@ -900,8 +890,11 @@ __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* f
     constexpr int T = 32 / G;
     const int lane = threadIdx.x & 31;
     GroupHead* head = wh + lane / G;
-    View V;
-    const bool active = has_track && setup_track<G>(A, head, ft, X, off, e, t, gl, gmask, V);
+    bool active;
+    {
+        View V0;
+        active = has_track && setup_track<G>(A, head, ft, X, off, e, t, gl, gmask, V0);
+    }
     if (gl == 0) {
         head->act = active;
         head->best = ~0ull;
@@ -910,6 +903,18 @@ __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* f
     }
     __syncwarp();
     warp_search<T, 0>(A, wh, ft, Q, X, off, lane);
+    // the group's view, from its shared state
+    View V;
+    V.h = head;
+    V.ft = ft;
+    V.X = X;
+    V.off = off;
+    V.S = A.S;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        V.hi[l] = head->hi[l];
+        V.lo[l] = head->lo[l];
+    }
     int best_nh = 0, best_dir = 0, best_pa = -1, best_pb = -1;
     float best_c2 = 0.f;
     bool rec = false;
