@@ -154,6 +154,9 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
         A.band_r[dir] = r;
         A.band_inv_r[dir] = r != 0.f ? 1.0f / r : 0.f;
         A.band_k1[dir] = r != 0.f ? (1.0f - r) / r : 0.f;
+        const float q = 1.0f - r;
+        A.band_inv_q[dir] = q != 0.f ? 1.0f / q : 0.f;
+        A.band_k2[dir] = q != 0.f ? r / q : 0.f;
     }
     A.x_cap = 0;
     A.split = 1;

@@ -63,6 +63,7 @@ struct FindArgs {
     int16_t* win;
     unsigned long long* status;
     float band_r[2], band_inv_r[2], band_k1[2];  // kink-band constants per direction
+    float band_inv_q[2], band_k2[2];               // 1 / (1 - r), r / (1 - r)
     uint32_t x_cap;              // hits of an event staged in shared memory
     int split;                   // blocks sharing one event's tracks
     // The normal matrix of the fit depends only on which layers carry a
@@ -348,6 +349,31 @@ __device__ __forceinline__ void kink_band(const FindArgs& A, float da, float& bl
         }
         blo = e0 - 1e-5f * (1.f + fabsf(e0));
         bhi = e1 + 1e-5f * (1.f + fabsf(e1));
+    }
+}
+
+// Band of d_a (first anchor) that can pass the kink cut for a given d_b:
+// |da (1 - r) + db r| <= tol_kink gives da within (+-tol_kink)/(1 - r) -
+// db r/(1 - r), widened far beyond float rounding like kink_band.
+template <int DIR>
+__device__ __forceinline__ void kink_band_rev(const FindArgs& A, float db, float& alo, float& ahi) {
+    constexpr int la = DIR ? 3 : 0;
+    const float q = 1.f - A.band_r[DIR];
+    alo = -INFINITY;
+    ahi = INFINITY;
+    if (fabsf(q) > 1e-3f) {
+        const float mag = (1.f + fabsf(db) + A.hw[la]) * (1.f + fabsf(A.band_r[DIR]));
+        const float eps = 1e-5f * mag;
+        const float c = db * A.band_k2[DIR];
+        const float w = (A.tol_kink + eps) * A.band_inv_q[DIR];
+        float e0 = -w - c, e1 = w - c;
+        if (e0 > e1) {
+            const float t = e0;
+            e0 = e1;
+            e1 = t;
+        }
+        alo = e0 - 1e-5f * (1.f + fabsf(e0));
+        ahi = e1 + 1e-5f * (1.f + fabsf(e1));
     }
 }
 
@@ -674,10 +700,13 @@ __device__ __forceinline__ unsigned long long tracklet_key(int nh, float chi2, i
 }
 
 // Fast path of one direction for all tracks of a warp with act set
-// (Sec. V-B).  The first anchors of those tracks are taken 32 at a time
-// across the whole warp; each lane finds its anchor's band of second
-// anchors, and the (anchor, second anchor) pairs join the warp's queue
-// (lane q appends pair q of the warp-wide prefix count).  Whenever 32 pairs
+// (Sec. V-B).  The second anchors of those tracks (the layer with the
+// narrower window) are taken 32 at a time across the whole warp; each lane
+// finds its hit's band of first anchors that can pass the kink cut, and the
+// (first anchor, second anchor) pairs join the warp's queue (lane q appends
+// pair q of the warp-wide prefix count).  The set of pairs is the one of the
+// sequential enumeration; its order does not matter here because every
+// tracklet carries its combined (first, second) index in its key.  Whenever 32 pairs
 // are queued they are evaluated exactly, one per lane; each track keeps the
 // minimum packed key of its valid tracklets, their count, the keys of the
 // first kListCap of them, and a record of the tracklet holding the minimum.
@@ -749,14 +778,15 @@ template <int T, int DIR>
 __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft, PairQueue* Q, const float* X,
                             const uint32_t* off, int lane) {
     constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
-    const int na = lane < T && wh[lane].act ? wh[lane].wunion[la][1] - wh[lane].wunion[la][0] : 0;
+    // the outer loop runs over the second-anchor layer (the narrower window)
+    const int na = lane < T && wh[lane].act ? wh[lane].wunion[lb][1] - wh[lane].wunion[lb][0] : 0;
     int pre = na;
 #pragma unroll
     for (int o = 1; o < T; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, pre, o);
         if (lane >= o) pre += v;
     }
-    // lane s < T holds the inclusive anchor prefix of slot s
+    // lane s < T holds the inclusive prefix of slot s
     const int n_anchor = __shfl_sync(0xffffffffu, pre, T - 1);
     int nq = 0;  // queued pairs (warp-uniform)
     for (int ab = 0; ab < n_anchor; ab += 32) {
@@ -765,7 +795,7 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
 #pragma unroll
         for (int s = 0; s < T; ++s) u += __shfl_sync(0xffffffffu, pre, s) <= ia;
         const int excl = __shfl_sync(0xffffffffu, pre, max(u - 1, 0)) * (u > 0);
-        int c = 0, p0 = 0, pa = 0;
+        int c = 0, p0 = 0, pb = 0;
         if (ia < n_anchor && wh[u].count <= kListCap) {
             const GroupHead* h = wh + u;
             View V;
@@ -777,14 +807,14 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             V.lo[la] = h->lo[la];
             V.hi[lb] = h->hi[lb];
             V.lo[lb] = h->lo[lb];
-            pa = h->wunion[la][0] + (ia - excl);
-            const float da = V.d(la, pa);
-            float blo, bhi;
-            kink_band<DIR>(A, da, blo, bhi);
-            const int wb1 = h->wunion[lb][1];
-            p0 = V.lower(lb, blo, A.hw[lb]);
+            pb = h->wunion[lb][0] + (ia - excl);
+            const float db = V.d(lb, pb);
+            float alo, ahi;
+            kink_band_rev<DIR>(A, db, alo, ahi);
+            const int wa1 = h->wunion[la][1];
+            p0 = V.lower(la, alo, A.hw[la]);
             int p1 = p0;
-            while (p1 < wb1 && V.d(lb, p1) <= bhi) ++p1;
+            while (p1 < wa1 && V.d(la, p1) <= ahi) ++p1;
             c = p1 - p0;
         }
         int incl = c;
@@ -805,13 +835,13 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             }
             j = min(j, 31);
             const int j_u = __shfl_sync(0xffffffffu, u, j);
-            const int j_pa = __shfl_sync(0xffffffffu, pa, j);
+            const int j_pb = __shfl_sync(0xffffffffu, pb, j);
             const int j_p0 = __shfl_sync(0xffffffffu, p0, j);
             const int j_ex = __shfl_sync(0xffffffffu, incl - c, j);
             const int m = min(32, n_pair - q0);
             if (lane < m) {
-                Q->pa[nq + lane] = j_pa;
-                Q->pb[nq + lane] = j_p0 + (q - j_ex);
+                Q->pa[nq + lane] = j_p0 + (q - j_ex);
+                Q->pb[nq + lane] = j_pb;
                 Q->u[nq + lane] = j_u;
             }
             nq += m;
