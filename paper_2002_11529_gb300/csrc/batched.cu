@@ -15,19 +15,30 @@
 
 namespace utc {
 
+// Shared memory of a block: big-bank bins, bank offsets, the event's
+// decoded x, then one region used in turn by the decode of an event (raw
+// stage, bank map, source map) and by its search (per-track state, pair
+// queues) -- an event's search starts after its decode and the next decode
+// after the search -- and the fit table.
 struct BatchedLayout {
-    size_t off_bytes, stage_byte0, sx_byte0, heads_byte0, queues_byte0, fit_byte0, total;
+    size_t off_bytes, sx_byte0, union_byte0, map_byte0, queues_byte0, fit_byte0, total;
 };
 
-__host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_words, uint32_t x_cap, int gpb,
-                                                       int warps) {
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_words, uint32_t x_cap,
+                                                       uint32_t map_cap, int gpb, int warps) {
     BatchedLayout L;
     L.off_bytes = (size_t)kBigWarps * kKeyBins * 4;
-    L.stage_byte0 = L.off_bytes + (((size_t)(B + 1) * 4 + 15) & ~(size_t)15);
-    L.sx_byte0 = L.stage_byte0 + (size_t)stage_words * 4 + 16;
-    L.heads_byte0 = L.sx_byte0 + (((size_t)x_cap * 4 + 15) & ~(size_t)15);
-    L.queues_byte0 = L.heads_byte0 + (size_t)gpb * sizeof(GroupHead);
-    L.fit_byte0 = L.queues_byte0 + (size_t)warps * sizeof(PairQueue);
+    L.sx_byte0 = L.off_bytes + align16((size_t)(B + 1) * 4);
+    L.union_byte0 = L.sx_byte0 + align16((size_t)x_cap * 4);
+    // decode view: stage (16 bytes of slack for its run-time alignment), maps
+    L.map_byte0 = L.union_byte0 + (size_t)stage_words * 4 + 16;
+    const size_t dec_end = L.map_byte0 + (size_t)map_cap * 2 * sizeof(uint16_t);
+    // search view: per-track state, then the pair queues
+    L.queues_byte0 = L.union_byte0 + align16((size_t)gpb * sizeof(GroupHead));
+    const size_t search_end = L.queues_byte0 + (size_t)warps * sizeof(PairQueue);
+    L.fit_byte0 = align16(dec_end > search_end ? dec_end : search_end);
     L.total = L.fit_byte0 + sizeof(FitTable);
     return L;
 }
@@ -47,20 +58,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
     const int gl = tid % G;
     const int lane = tid & 31;
     const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, gpb, NT / 32);
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, gpb, NT / 32);
     DecodeSmem sm;
     sm.bigcnt = reinterpret_cast<uint32_t*>(smem);
     sm.off = reinterpret_cast<uint32_t*>(smem + L.off_bytes);
-    size_t sb = L.stage_byte0;
+    size_t sb = L.union_byte0;
     sb += (16u - ((smem_u32(smem) + (uint32_t)sb) & 15u)) & 15u;
     sm.stage = reinterpret_cast<uint32_t*>(smem + sb);
     sm.mbar = &mbar;
     sm.s_base = &s_base;
     sm.warp_tot = warp_tot;
-    sm.bmap = nullptr;      // per-hit path: shared memory holds the event's x for the search
-    sm.srcmap = nullptr;
+    sm.bmap = D.map_cap ? reinterpret_cast<uint16_t*>(smem + L.map_byte0) : nullptr;
+    sm.srcmap = sm.bmap ? sm.bmap + D.map_cap : nullptr;
     float* sx = reinterpret_cast<float*>(smem + L.sx_byte0);
-    GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.heads_byte0);
+    GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.union_byte0);
     PairQueue* Q = reinterpret_cast<PairQueue*>(smem + L.queues_byte0) + tid / 32;
     FitTable* ft = reinterpret_cast<FitTable*>(smem + L.fit_byte0);
     stage_fit_table(A, ft);  // read after the loop's first barrier
@@ -96,7 +107,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
 template <int G, int NT>
 static int launch_batched(const DecodeArgs& D, const FindArgs& A, int num_sms, cudaStream_t st) {
     const int B = 4 * D.S;
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, NT / G, NT / 32);
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, NT / G, NT / 32);
     const size_t smem = L.total;
     auto kern = ut_batched_kernel<G, NT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -185,8 +196,8 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     D.status = ctx->d_status;
     D.stage_words = (uint32_t)stage_words;
-    D.map_cap = 0;
-    D.vec_ok = 0;
+    D.map_cap = 4 * S <= 1024 ? kMapCapDefault : 0;  // sorted bank-map path (bank and rank share 16 bits)
+    D.vec_ok = hits_aligned16(hits_out);
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
     switch (tpw) {
         case 1: return launch_batched_g<32>(D, A, block, ctx->num_sms, st);

@@ -171,11 +171,6 @@ static size_t decode_smem_bytes(int B, bool sort, uint32_t stage_words, uint32_t
     return head + (size_t)stage_words * 4 + (size_t)map_cap * (sort ? 2 : 1) * sizeof(uint16_t);
 }
 
-static int outputs_aligned(const ut_hits* h) {
-    const uintptr_t m = (uintptr_t)h->x | (uintptr_t)h->z | (uintptr_t)h->sector | (uintptr_t)h->layer |
-                        (uintptr_t)h->id;
-    return (m & 15u) == 0;
-}
 
 }  // namespace utc
 
@@ -220,7 +215,7 @@ extern "C" int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_word
     a.status = ctx->d_status;
     a.stage_words = kStageWordsDefault;
     a.map_cap = B <= 65536 ? kMapCapDefault : 0;
-    a.vec_ok = outputs_aligned(out);
+    a.vec_ok = hits_aligned16(out);
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
     const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words, a.map_cap);
     cudaError_t err;
@@ -339,7 +334,7 @@ extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw,
     a.status = d_status;
     a.stage_words = kStageWordsDefault;
     a.map_cap = B <= 65536 ? kMapCapDefault : 0;
-    a.vec_ok = outputs_aligned(out);
+    a.vec_ok = hits_aligned16(out);
     // the array keeps the previous call's contents: clear the counter and the
     // look-back state of the events used here
     if (cudaMemsetAsync(scratch, 0, 16 + (size_t)n_events * sizeof(unsigned long long), st) != cudaSuccess)

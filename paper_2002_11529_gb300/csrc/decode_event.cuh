@@ -51,6 +51,13 @@ struct DecodeArgs {
     int vec_ok;                  // output arrays are 16-byte aligned
 };
 
+// All five output arrays start on a 16-byte boundary (vector stores allowed).
+inline int hits_aligned16(const ut_hits* h) {
+    const uintptr_t m = (uintptr_t)h->x | (uintptr_t)h->z | (uintptr_t)h->sector | (uintptr_t)h->layer |
+                        (uintptr_t)h->id;
+    return (m & 15u) == 0;
+}
+
 struct HitOut {
     float* x;
     float* z;
