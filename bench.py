@@ -6,6 +6,10 @@ sort, window search, tracklet finding, q/p fit) over one batch of seeded
 synthetic events whose shapes follow the paper's workloads (the LHCb
 minbias samples themselves are not available).  Default workload: 1000
 events, 4 planes x 256 sectors, 4000 hits and 200 VELO tracks per event.
+Default form: the persistent decode + Compass kernel (one launch replayed
+from a CUDA graph) with its launch shape picked by the autotuner; --form
+fused (sorted decode, then compass_find) and --form plain (decode, sort,
+find, fit) time the per-kernel forms.
 
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
 launching stream, the L2 flushed (256 MB write) before every step, bracketed
@@ -46,8 +50,9 @@ def parse():
     ap.add_argument("--workload", default="plain", choices=list(WORKLOADS))
     ap.add_argument("--events", type=int, default=None,
                     help="first N events of the workload's generator (smaller cases for profiling)")
-    ap.add_argument("--form", default="fused", choices=["batched", "fused", "plain"])
-    ap.add_argument("--autotune", action="store_true", help="pick the batched launch shape by a sweep")
+    ap.add_argument("--form", default="batched", choices=["batched", "fused", "plain"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched form: use --tracks-per-warp/--block instead of the autotuner's pick")
     ap.add_argument("--x-cap", type=int, default=8192)
     ap.add_argument("--tracks-per-warp", type=int, default=8)
     ap.add_argument("--block", type=int, default=256)
@@ -333,7 +338,7 @@ def main():
             "batched": ["ut_run_batched"]}[args.form]
     cfg = g.LaunchConfig(tpw, blk, args.x_cap, 8192)
     tune_table = None
-    if args.form == "batched" and args.autotune:
+    if args.form == "batched" and not args.no_autotune:
         from paper_2002_11529_gb300 import autotune
         cfg, tune_table = autotune.autotune(pipe, reps=3, flush=flush)
     runner = g.GraphRunner(pipe, cfg) if args.form == "batched" else None
