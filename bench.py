@@ -62,6 +62,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest `value` over all ranks (the job's time is its slowest
+    rank's); `value` itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_events_per_s(world, events_per_rank, steps, seconds):
+    """Whole-job throughput: every rank processes its own `events_per_rank`
+    per step (weak scaling), the time is the slowest rank's."""
+    return world * events_per_rank * steps / seconds
+
+
 def make_batch(wl, rank, n_events=None):
     import synth
     c = dict(WORKLOADS[wl])
@@ -435,12 +452,8 @@ def main():
     ctx.check(stream, "timed region")
     step_ms = [step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(args.steps)]
     kern_ms = {kern[i]: [evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)] for i in range(nk)}
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * E * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), dist)
+    value = job_events_per_s(world, E, args.steps, tot_ms / 1e3)
 
     # ---- end to end through host buffers ------------------------------------
     h_raw = pipe.raw.cpu().pin_memory()
@@ -476,22 +489,16 @@ def main():
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     barrier()
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist)
     ctx.check(stream, "e2e")
-    e2e_serial = world * E * args.steps / (e2e_ms / 1e3)
+    e2e_serial = job_events_per_s(world, E, args.steps, e2e_ms / 1e3)
     e2e = {"value": e2e_serial, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "copy in, step, copy out on one stream, one step at a time (CUDA events)"}
     if args.form == "batched":
         # the persistent form through the serving engine: steps overlap
         wall, sh2d, sd2h = e2e_through_server(g, batch, params, cfg, args.steps)
-        if dist is not None:
-            t = torch.tensor([wall], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": world * E * args.steps / wall, "unit": "events/s", "h2d_bytes_per_step": sh2d,
+        wall = max_over_ranks(wall, dist)
+        e2e = {"value": job_events_per_s(world, E, args.steps, wall), "unit": "events/s", "h2d_bytes_per_step": sh2d,
                "d2h_bytes_per_step": sd2h,
                "how": "ut_server: each step one request of the whole batch from page-locked host memory, "
                       "up to 4 in flight on 4 stream slots; host wall clock",
