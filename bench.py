@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the uneven-workload form comparison and the serving measurement")
+                    help="skip the uneven-workload form comparison, serving and alignment measurements")
     return ap.parse_args()
 
 
@@ -302,6 +302,61 @@ def measure_serving(g, params, loads=(0.5, 0.8, 0.95)):
             res[f"load_{int(round(f * 100))}"] = {k: summ[k] for k in ("events_per_s", "p50_ms", "p99_ms",
                                                                        "queue_p50_ms", "errors")}
         res["arena_peak_bytes"] = sv.stats()["arena_peak"]
+    return res
+
+
+def measure_alignment(g, params, reps=10):
+    """Alignment on the 100k-track, 4 x 256-sector set (3072 parameters):
+    device times of one chi2 + adjoint pass (gradients and Gauss-Newton
+    blocks), one refit, one reduced Hessian-vector product, and the 20-step
+    solve (CUDA events, L2 flushed before each timed call)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2002_11529_gb300 import align
+    a = synth.generate_alignment(100_000, 256, seed=4)
+    b = a.batch
+    ctx = g.Context(b.geom)
+    raw, ev = g.upload_raw(b.raw, b.ev_off)
+    nw = int(b.ev_off[-1])
+    hits = g.HitBuffers.allocate(2 * nw, b.n_events, b.geom.n_sectors)
+    g.ut_decode(ctx, raw, nw, ev, b.n_events, hits, sorted_=False)
+    t = lambda arr, dt: torch.from_numpy(np.ascontiguousarray(arr).view(dt)).cuda()
+    velo = g.VeloBuffers(t(a.x, np.float32), t(a.y, np.float32), t(a.tx, np.float32), t(a.ty, np.float32),
+                         torch.zeros(a.n_tracks, dtype=torch.uint8, device="cuda"),
+                         torch.zeros(2, dtype=torch.int32, device="cuda"))
+    prob = align.AlignmentProblem(ctx, hits, t(a.track_hits, np.int32), velo, params)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    al = torch.from_numpy(a.align_true().astype(np.float32)).cuda()
+    th = prob.refit(al)
+    v = torch.ones((4 * b.geom.n_sectors, 3), dtype=torch.float64, device="cuda")
+
+    def timed(fn, n=reps):
+        ms = []
+        for _ in range(n + 1):
+            flush.add_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms[1:]))
+
+    res = {"tracks": a.n_tracks, "parameters": 3 * 4 * b.geom.n_sectors,
+           "chi2_and_adjoint_ms": timed(lambda: prob.chi2(th, al, grads=True)),
+           "refit_ms": timed(lambda: prob.refit(al)),
+           "hvp_ms": timed(lambda: prob.hvp(th, al, v))}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    est, hist = align.solve_alignment(prob, steps=20)
+    e1.record()
+    e1.synchronize()
+    c_true = prob.chi2(prob.refit(al), al)[0].item()
+    res["solve_20_steps_ms"] = e0.elapsed_time(e1)
+    res["chi2_per_track"] = {"start": hist[0] / a.n_tracks, "after_20_steps": hist[-1] / a.n_tracks,
+                             "truth": c_true / a.n_tracks}
+    ctx.check(what="alignment")
     return res
 
 
@@ -550,6 +605,7 @@ def main():
     if not args.no_variants and world == 1:
         line["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
         line["serving"] = measure_serving(g, params)
+        line["alignment"] = measure_alignment(g, params)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
     print(json.dumps(line), flush=True)
