@@ -347,6 +347,7 @@ def measure_alignment(g, params, reps=10):
            "chi2_and_adjoint_ms": timed(lambda: prob.chi2(th, al, grads=True)),
            "refit_ms": timed(lambda: prob.refit(al)),
            "hvp_ms": timed(lambda: prob.hvp(th, al, v))}
+    align.solve_alignment(prob, steps=20)  # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     est, hist = align.solve_alignment(prob, steps=20)

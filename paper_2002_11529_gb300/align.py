@@ -91,16 +91,22 @@ class Chi2Alignment(torch.autograd.Function):
 
 
 def _block_inverse(h6: torch.Tensor) -> torch.Tensor:
-    """Inverse of the per-sector 3x3 blocks (zero for sectors without hits)."""
+    """Inverse of the per-sector symmetric 3x3 blocks [a b c; b d e; c e f]
+    (h6 = a, b, c, d, e, f) by cofactors in double; zero for sectors without
+    hits (a == 0) or a singular block.  Returns [4S, 3, 3]."""
     h = h6.to(torch.float64)
-    H = torch.stack([torch.stack([h[:, 0], h[:, 1], h[:, 2]], -1),
-                     torch.stack([h[:, 1], h[:, 3], h[:, 4]], -1),
-                     torch.stack([h[:, 2], h[:, 4], h[:, 5]], -1)], -2)
-    used = h[:, 0] > 0
-    eye = torch.eye(3, dtype=torch.float64, device=h.device)
-    Hs = torch.where(used[:, None, None], H, eye)
-    inv = torch.linalg.inv(Hs)
-    return torch.where(used[:, None, None], inv, torch.zeros_like(inv))
+    a, b, c, d, e, f = (h[:, i] for i in range(6))
+    A = d * f - e * e
+    Bc = c * e - b * f
+    C = b * e - c * d
+    D = a * f - c * c
+    E = b * c - a * e
+    F = a * d - b * b
+    det = a * A + b * Bc + c * C
+    ok = (a > 0) & (det != 0)
+    r = torch.where(ok, 1.0 / torch.where(ok, det, torch.ones_like(det)), torch.zeros_like(det))
+    inv = torch.stack([torch.stack([A, Bc, C], -1), torch.stack([Bc, D, E], -1), torch.stack([C, E, F], -1)], -2)
+    return inv * r[:, None, None]
 
 
 def solve_alignment(problem: AlignmentProblem, steps: int = 20, relinearize_every: int = 10,
