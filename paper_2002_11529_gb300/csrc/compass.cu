@@ -2,10 +2,11 @@
 //
 // compass_find: event-centric.  A block stages one event's hit x and bank
 // offsets in shared memory (read once, reused by all of the event's
-// tracks), then its lane groups (G = 32/16/8 lanes: 1/2/4 tracks per warp)
-// run the per-track window search and tracklet finding of
-// compass_track.cuh.  An event's tracks may be split over `split` blocks so
-// that the grid has enough independent work.
+// tracks), then its warps (G = 32/16/8/4 lanes per track: 1/2/4/8 tracks
+// per warp) run the window search and tracklet finding of
+// compass_track.cuh on the tracks of one contiguous part of the event: the
+// part's tracks are dealt to the warps in equal contiguous shares.  One
+// block per part, so the hardware balances events of different sizes.
 //
 // compass_fit: the closed-form p-kick fit of given hits (one thread/track).
 
@@ -31,26 +32,26 @@ __global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A)
     float* sx = reinterpret_cast<float*>(ft + 1);
     PairQueue* Q = queues + threadIdx.x / 32;
     stage_fit_table(A, ft);
-    const long long units = (long long)A.n_events * A.split;
-    for (long long v = blockIdx.x; v < units; v += gridDim.x) {
-        const int e = (int)(v / A.split), part = (int)(v % A.split);
-        __syncthreads();  // the previous event's readers are done
-        const uint32_t hb = A.hit_off[(size_t)e * B];
-        for (int i = threadIdx.x; i <= B; i += nt) soff[i] = A.hit_off[(size_t)e * B + i] - hb;
-        const uint32_t he = A.hit_off[(size_t)(e + 1) * B] - hb;
-        const bool staged = he <= A.x_cap;
-        if (staged)
-            for (uint32_t i = threadIdx.x; i < he; i += nt) sx[i] = __ldg(A.hx + hb + i);
-        __syncthreads();
-        const float* X = staged ? sx : A.hx + hb;
-        const uint32_t t0 = A.trk_off[e], t1 = A.trk_off[e + 1];
-        const uint32_t step = (uint32_t)A.split * gpb;
-        // warp-uniform loop: the warp's first group has track tw
-        const int gw = g - (lane / G);  // first group of this warp
-        for (uint32_t tw = t0 + (uint32_t)part * gpb + gw; tw < t1; tw += step) {
-            const uint32_t t = tw + (uint32_t)(g - gw);
-            compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t, t < t1, gl, gmask);
-        }
+    constexpr int T = 32 / G;
+    const int W = nt / 32, w = threadIdx.x / 32;
+    const int e = (int)(blockIdx.x / A.split), part = (int)(blockIdx.x % A.split);
+    const uint32_t hb = A.hit_off[(size_t)e * B];
+    for (int i = threadIdx.x; i <= B; i += nt) soff[i] = A.hit_off[(size_t)e * B + i] - hb;
+    const uint32_t he = A.hit_off[(size_t)(e + 1) * B] - hb;
+    const bool staged = he <= A.x_cap;
+    if (staged)
+        for (uint32_t i = threadIdx.x; i < he; i += nt) sx[i] = __ldg(A.hx + hb + i);
+    __syncthreads();
+    const float* X = staged ? sx : A.hx + hb;
+    // this block's part of the event's tracks, then this warp's share of it
+    const uint32_t t0 = A.trk_off[e], n = A.trk_off[e + 1] - t0;
+    const uint32_t pa = (uint32_t)((uint64_t)n * part / A.split), pb = (uint32_t)((uint64_t)n * (part + 1) / A.split);
+    const uint32_t len = pb - pa, q = (len + W - 1) / W;
+    const uint32_t wa = pa + min(len, q * w), wb = pa + min(len, q * (w + 1));
+    const int gw = g - (lane / G);  // first group of this warp
+    for (uint32_t tw = wa; tw < wb; tw += T) {
+        const uint32_t k = tw + (uint32_t)(g - gw);
+        compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t0 + k, k < wb, gl, gmask);
     }
 }
 
@@ -209,10 +210,6 @@ template <int G>
 static int launch_find(FindArgs A, int block, int num_sms, cudaStream_t st) {
     const int gpb = block / G;
     const int B = 4 * A.S;
-    // split an event's tracks over blocks so that about two tracks per lane
-    // group remain per block
-    const double tpe = A.n_events > 0 ? (double)A.n_tracks / A.n_events : 0.0;
-    A.split = (int)fmax(1.0, fmin(64.0, tpe / (2.0 * gpb)));
     A.x_cap = 8192;
     const size_t off_bytes = ((size_t)(B + 1) * 4 + 15) & ~(size_t)15;
     const size_t smem = off_bytes + (size_t)gpb * sizeof(GroupHead) + (size_t)(block / 32) * sizeof(PairQueue) +
@@ -220,9 +217,15 @@ static int launch_find(FindArgs A, int block, int num_sms, cudaStream_t st) {
     if (cudaFuncSetAttribute(compass_event_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return UT_ERR_CUDA;
+    // One block per part of an event: an event's tracks are split so that
+    // about two warp calls of tracks remain per warp (tracks of one warp call
+    // share its fixed setup and resolution latency).
+    const double tpe = A.n_events > 0 ? (double)A.n_tracks / A.n_events : 0.0;
+    const int best_s = (int)fmax(1.0, fmin(64.0, tpe / (2.0 * gpb)));
+    A.split = best_s;
     const long long units = (long long)A.n_events * A.split;
-    const long long cap = (long long)num_sms * 16;
-    const int grid = (int)(units < cap ? units : cap);
+    if (units > 0x7fffffffll) return UT_ERR_ARG;
+    const int grid = (int)units;
     compass_event_kernel<G><<<grid, block, smem, st>>>(A);
     return check_cuda(cudaGetLastError());
 }
