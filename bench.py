@@ -277,11 +277,12 @@ def time_forms_on_uneven_workload(g, params, flush, steps=5):
     return out
 
 
-def measure_serving(g, params, loads=(0.5, 0.8, 0.95)):
+def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95)):
     """Serving: requests of 64-4096 events (log-uniform, plain-workload
     occupancy) through the continuous-batching engine, 40 GB budget,
-    8 stream slots: sustained peak (all submitted at once), then Poisson
-    arrivals at fractions of that peak; p50/p99 request latency."""
+    8 stream slots, persistent launch shape `cfg`: sustained peak (all
+    submitted at once), then Poisson arrivals at fractions of that peak;
+    p50/p99 request latency."""
     import numpy as np
     import synth
     from paper_2002_11529_gb300 import serve
@@ -291,8 +292,9 @@ def measure_serving(g, params, loads=(0.5, 0.8, 0.95)):
                for i, n in enumerate(sizes)]
     reqs = [serve.HostRequest.from_batch(b) for b in batches]
     res = {"requests_per_level": 2 * len(reqs), "events_per_request": "64-4096 log-uniform",
-           "budget_bytes": 40 << 30, "slots": 8}
-    with serve.Server(batches[0].geom, params, budget_bytes=40 << 30, n_slots=8) as sv:
+           "budget_bytes": 40 << 30, "slots": 8,
+           "launch": None if cfg is None else {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block}}
+    with serve.Server(batches[0].geom, params, budget_bytes=40 << 30, n_slots=8, cfg=cfg) as sv:
         serve.run_closed_loop(sv, reqs)            # warm-up
         peak, _ = serve.run_closed_loop(sv, reqs + reqs)
         res["peak_events_per_s"] = peak["events_per_s"]
@@ -605,7 +607,7 @@ def main():
     }
     if not args.no_variants and world == 1:
         line["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
-        line["serving"] = measure_serving(g, params)
+        line["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
         line["alignment"] = measure_alignment(g, params)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
