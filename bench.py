@@ -363,6 +363,41 @@ def measure_alignment(g, params, reps=10):
     return res
 
 
+def physics_sweep(g, batch, params, reps=5):
+    """The paper's trade-off table on the synthetic workload: for
+    n_sectors in {1, 3, 5} and n_candidates in {1, 2, 4, 8, 16}, the track
+    finding efficiency and fake rate on generator truth, and the events/s
+    of the sorted decode + compass_find (8 tracks per warp, L2 flushed)."""
+    import numpy as np
+    import torch
+    from paper_2002_11529_gb300 import physics
+    ctx = g.Context(batch.geom)
+    pipe = g.Pipeline(ctx, batch, params)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    E = batch.n_events
+    out = []
+    for n_sec in (1, 3, 5):
+        for n_cand in (1, 2, 4, 8, 16):
+            p = params.replace(n_sectors=n_sec, n_candidates=n_cand)
+            ms = []
+            for r in range(reps + 1):
+                flush.add_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, True, pipe.workspace)
+                g.compass_find(ctx, pipe.hits_a, pipe.velo, E, p, pipe.tracks, tracks_per_warp=8)
+                e1.record()
+                e1.synchronize()
+                if r:
+                    ms.append(e0.elapsed_time(e1))
+            ctx.check(what="physics sweep")
+            ev = physics.evaluate(batch, g.tracks_to_numpy(pipe.tracks, batch.n_tracks))
+            out.append({"n_sectors": n_sec, "n_candidates": n_cand, "events_per_s": E / float(np.median(ms)) * 1e3,
+                        "efficiency": ev["efficiency"], "fake_rate": ev["fake_rate"], "clone_rate": ev["clone_rate"]})
+    return {"workload": "the bench workload; efficiency on generator truth (Sec. II-C definitions)",
+            "reconstructible": ev["reconstructible"], "table": out}
+
+
 def e2e_through_server(g, batch, params, cfg, steps, n_slots=4):
     """End to end through the serving engine: every step is one request of
     the whole batch (host inputs in page-locked memory copied in, one
@@ -609,6 +644,7 @@ def main():
         line["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
         line["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
         line["alignment"] = measure_alignment(g, params)
+        line["physics_sweep"] = physics_sweep(g, batch, params)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
     print(json.dumps(line), flush=True)
