@@ -102,6 +102,9 @@ typedef struct compass_params {
     float sigma_tx_prior;   /* VELO tx prior, > 0                             */
     float z_kink;           /* kink plane of the magnet kick (mm)             */
     float kick_k;           /* kick: dx = kick_k*(q/p)*(z - z_kink)           */
+    int gec_max_hits;       /* Global Event Cut (Sec. VI): the tracks of an event
+                             * with more UT hits are not searched (found = 0,
+                             * windows -1); 0 = no cut                        */
 } compass_params;
 
 /* One output slot per VELO track (Sec. V-B output, placed at the track's
@@ -224,6 +227,45 @@ int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int 
  */
 int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint32_t n_tracks,
                 const compass_params* p, compass_tracks* inout, void* stream);
+
+/*
+ * Consolidated tracks: the found tracks only, in (event, VELO track) order,
+ * in coalesced arrays (the prefix sum and consolidation steps the paper runs
+ * after the tracking for the algorithms that take UT tracks as input,
+ * Sec. VI).  All device pointers, owned by the caller; capacity = rows
+ * available.
+ */
+typedef struct ut_tracks_compact {
+    int32_t* hit;           /* [N][4] global hit index per layer, -1 = none  */
+    float* qop;
+    float* chi2;
+    float* x;
+    float* tx;
+    uint8_t* nhits;
+    uint32_t* velo;         /* VELO track index of each row                  */
+    uint32_t capacity;
+} ut_tracks_compact;
+
+/* Bytes of device scratch that ut_consolidate needs for n_events (a work
+ * counter and the per-event look-back state): 16 + 8 * n_events. */
+size_t ut_consolidate_workspace_size(int n_events);
+
+/*
+ * ut_consolidate -- prefix sum of the found tracks over the events and
+ * consolidation (Sec. VI).  d_trk_off: u32[n_events + 1] track offsets of
+ * the events (as velo_tracks.trk_off); in: the track slots compass_find or
+ * ut_run_batched wrote (found, hit, qop, chi2, x, tx, nhits are read).
+ * Writes the found tracks, in order, to out (rows [0, N)) and
+ * d_out_off[e] = first row of event e, d_out_off[n_events] = N.  One
+ * single-pass kernel (one block per event, decoupled look-back).
+ * Workspace: >= ut_consolidate_workspace_size(n_events) bytes, 16-byte
+ * aligned; cleared on `stream` before use.  N > out->capacity records
+ * UT_ERR_CAPACITY in the status word (rows past the capacity are not
+ * written; d_out_off is complete).  n_events == 0 writes d_out_off[0] = 0.
+ */
+int ut_consolidate(ut_ctx* ctx, const uint32_t* d_trk_off, int n_events, const compass_tracks* in,
+                   ut_tracks_compact* out, uint32_t* d_out_off, void* d_workspace, size_t workspace_bytes,
+                   void* stream);
 
 /* Launch shape of the batched form (0 in a field = its default). */
 typedef struct ut_launch_config {

@@ -47,7 +47,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("n_sectors", ctypes.c_int), ("n_candidates", ctypes.c_int)] + [
         (n, ctypes.c_float) for n in ("qop_max", "tol_win", "tol_kink", "tol_col", "tol_slope",
                                       "chi2ndof_max", "sigma_hit", "sigma_x_prior",
-                                      "sigma_tx_prior", "z_kink", "kick_k")]
+                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int)]
 
 
 def lib():
@@ -284,6 +284,20 @@ def run_batch(batch, params, n_threads=0, want_windows=False):
     tr = compass(hits.x, hits.hit_off, batch.n_events, batch.geom, Velo(batch), params,
                  want_windows=want_windows, n_threads=n_threads)
     return hits, tr
+
+
+def consolidate(tracks, trk_off):
+    """Prefix sum and consolidation (Sec. VI): the found tracks, in (event,
+    VELO track) order, and the first row of every event.  Written out by
+    its definition: the found tracks' indices, and the count of found
+    tracks before each event's first track."""
+    found = np.asarray(tracks["found"] if isinstance(tracks, dict) else tracks.found).astype(bool)
+    get = (lambda k: tracks[k]) if isinstance(tracks, dict) else (lambda k: getattr(tracks, k))
+    idx = np.nonzero(found)[0]
+    before = np.concatenate([[0], np.cumsum(found, dtype=np.int64)])
+    out = {k: np.asarray(get(k))[idx] for k in ("hit", "qop", "chi2", "x", "tx", "nhits")}
+    out["velo"] = idx.astype(np.uint32)
+    return out, before[np.asarray(trk_off, np.int64)].astype(np.uint32)
 
 
 def align_chi2(hits, track_hits, geom, velo, params, align, theta, grads=True):

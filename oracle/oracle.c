@@ -258,6 +258,7 @@ typedef struct {
     int n_sectors, n_candidates;
     float qop_max, tol_win, tol_kink, tol_col, tol_slope, chi2ndof_max;
     float sigma_hit, sigma_x_prior, sigma_tx_prior, z_kink, kick_k;
+    int gec_max_hits; /* Global Event Cut (Sec. VI): events with more hits are not searched */
 } orc_params;
 
 typedef struct {
@@ -441,7 +442,7 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
     set_threads(n_threads);
     const int S = g->S, B = 4 * S;
     const int nsec = p->n_sectors;
-    if (nsec < 1 || nsec > 5 || p->n_candidates < 1) return ORC_ERR_ARG;
+    if (nsec < 1 || nsec > 5 || p->n_candidates < 1 || p->gec_max_hits < 0) return ORC_ERR_ARG;
     static const int slot_off[5] = {0, -1, 1, -2, 2};
     const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
     const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
@@ -463,6 +464,8 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
         range_t R[4] = {{0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}};
         float* dv[4] = {NULL, NULL, NULL, NULL};
         int dcap[4] = {0, 0, 0, 0};
+        const uint32_t ev_hits = hit_off[(size_t)(e + 1) * B] - hit_off[(size_t)e * B];
+        const int cut = p->gec_max_hits > 0 && ev_hits > (uint32_t)p->gec_max_hits;
         for (uint32_t tr = trk_off[e]; tr < trk_off[e + 1]; ++tr) {
             double mm = INFINITY;
             for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = -1;
@@ -471,8 +474,9 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             if (win)
                 for (int k = 0; k < 4 * nsec * 2; ++k) win[(size_t)tr * 4 * nsec * 2 + k] = -1;
 
-            /* Valid-track filter (Sec. V-A): not backward, in acceptance. */
-            if (vflags[tr] & 1u) { near_m[tr] = mm; continue; }
+            /* Global Event Cut, then the valid-track filter (Sec. V-A): not
+             * backward, in acceptance. */
+            if (cut || (vflags[tr] & 1u)) { near_m[tr] = mm; continue; }
             double u[4];
             float uhi[4], ulo[4];
             extrapolate(g, vx[tr], vy[tr], vtx[tr], vty[tr], u, uhi, ulo);

@@ -26,7 +26,7 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPA
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
-           "ut_align_refit", "ut_align_hvp")
+           "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate")
 
 
 class UtGeometry(ctypes.Structure):
@@ -50,11 +50,16 @@ class CompassParamsC(ctypes.Structure):
     _fields_ = [("n_sectors", ctypes.c_int), ("n_candidates", ctypes.c_int)] + [
         (n, ctypes.c_float) for n in ("qop_max", "tol_win", "tol_kink", "tol_col", "tol_slope",
                                       "chi2ndof_max", "sigma_hit", "sigma_x_prior",
-                                      "sigma_tx_prior", "z_kink", "kick_k")]
+                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int)]
 
 
 class CompassTracksC(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found")]
+
+
+class UtTracksCompactC(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "velo")] + [
+        ("capacity", ctypes.c_uint32)]
 
 
 class LaunchConfigC(ctypes.Structure):
@@ -105,6 +110,8 @@ def lib():
                 "ut_decode_noalloc": ([P, P, U64, P, I, P, I, P, P], I),
                 "ut_run_batched": ([P, P, U64, P, I, P, U32, P, P, P, P, P, SZ, P], I),
                 "ut_align_workspace_size": ([I], SZ),
+                "ut_consolidate_workspace_size": ([I], SZ),
+                "ut_consolidate": ([P, P, I, P, P, P, P, SZ, P], I),
                 "ut_align_chi2": ([P, P, P, P, U32, P, P, P, P, P, P, P, P, SZ, P], I),
                 "ut_align_refit": ([P, P, P, P, U32, P, P, P, P], I),
                 "ut_align_hvp": ([P, P, P, P, U32, P, P, P, P, P, P], I),
@@ -272,6 +279,34 @@ class TrackBuffers:
         return c
 
 
+@dataclasses.dataclass
+class CompactTracks:
+    """Consolidated found tracks (rows in (event, VELO track) order)."""
+    hit: torch.Tensor
+    qop: torch.Tensor
+    chi2: torch.Tensor
+    x: torch.Tensor
+    tx: torch.Tensor
+    nhits: torch.Tensor
+    velo: torch.Tensor
+    capacity: int
+
+    @staticmethod
+    def allocate(capacity, device="cuda"):
+        n = max(int(capacity), 1)
+        f = lambda: torch.empty(n, dtype=torch.float32, device=device)
+        return CompactTracks(torch.empty((n, 4), dtype=torch.int32, device=device), f(), f(), f(), f(),
+                             torch.empty(n, dtype=torch.uint8, device=device),
+                             torch.empty(n, dtype=torch.int32, device=device), int(capacity))
+
+    def struct(self) -> UtTracksCompactC:
+        c = UtTracksCompactC()
+        for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "velo"):
+            setattr(c, n, getattr(self, n).data_ptr())
+        c.capacity = self.capacity
+        return c
+
+
 def decode_workspace_size(n_events: int) -> int:
     return int(lib().ut_decode_workspace_size(int(n_events)))
 
@@ -380,6 +415,32 @@ def hits_to_numpy(h: HitBuffers, n=None):
                 sector=h.sector[:n].cpu().numpy().view(np.uint16),
                 layer=h.layer[:n].cpu().numpy(), id=h.id[:n].cpu().numpy().view(np.uint32),
                 hit_off=off)
+
+
+def consolidate_workspace_size(n_events: int) -> int:
+    return int(lib().ut_consolidate_workspace_size(int(n_events)))
+
+
+def ut_consolidate(ctx, trk_off, n_events, tracks: TrackBuffers, out: CompactTracks, out_off,
+                   workspace=None, stream=None):
+    """Found tracks of `tracks` -> consecutive rows of `out`, in (event, VELO
+    track) order; out_off (int32 device tensor, n_events + 1) = first row of
+    each event, then the total."""
+    ws_bytes = consolidate_workspace_size(n_events)
+    if workspace is None:
+        workspace = torch.empty((ws_bytes + 15) // 16 * 4, dtype=torch.int32, device=out_off.device)
+    tin = tracks.struct()
+    tout = out.struct()
+    _check(lib().ut_consolidate(ctx.handle, _ptr(trk_off), int(n_events), ctypes.byref(tin), ctypes.byref(tout),
+                                _ptr(out_off), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                _stream(stream)), "ut_consolidate")
+    return workspace
+
+
+def compact_to_numpy(c: CompactTracks, n):
+    return dict(hit=c.hit[:n].cpu().numpy(), qop=c.qop[:n].cpu().numpy(), chi2=c.chi2[:n].cpu().numpy(),
+                x=c.x[:n].cpu().numpy(), tx=c.tx[:n].cpu().numpy(), nhits=c.nhits[:n].cpu().numpy(),
+                velo=c.velo[:n].cpu().numpy().view(np.uint32))
 
 
 def tracks_to_numpy(t: TrackBuffers, n):

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
         const unsigned long long base = s_base;
         if (base + total > (unsigned long long)D.capacity) continue;  // reported by decode_event
         const float* X = total <= A.x_cap ? sx : D.x + base;
+        const bool search = A.gec == 0 || total <= (uint32_t)A.gec;  // Global Event Cut
         // the event's tracks dealt to the warps in equal contiguous shares
         constexpr int T = 32 / G, W = NT / 32;
         const uint32_t t0 = A.trk_off[e], n = A.trk_off[e + 1] - t0;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
         const int gw = g - (lane / G);  // first group of this warp
         for (uint32_t tw = wa; tw < wb; tw += T) {
             const uint32_t k = tw + (uint32_t)(g - gw);
-            compass_warp<G>(A, heads + gw, ft, Q, X, sm.off, (uint32_t)base, e, t0 + k, k < wb, gl, gmask);
+            compass_warp<G>(A, heads + gw, ft, Q, X, sm.off, (uint32_t)base, e, t0 + k, k < wb, search, gl, gmask);
         }
     }
     drain_stage(sm, phase, tma_ok);

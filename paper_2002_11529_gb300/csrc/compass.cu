@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A)
         for (uint32_t i = threadIdx.x; i < he; i += nt) sx[i] = __ldg(A.hx + hb + i);
     __syncthreads();
     const float* X = staged ? sx : A.hx + hb;
+    const bool search = A.gec == 0 || he <= (uint32_t)A.gec;  // Global Event Cut
     // this block's part of the event's tracks, then this warp's share of it
     const uint32_t t0 = A.trk_off[e], n = A.trk_off[e + 1] - t0;
     const uint32_t pa = (uint32_t)((uint64_t)n * part / A.split), pb = (uint32_t)((uint64_t)n * (part + 1) / A.split);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A)
     const int gw = g - (lane / G);  // first group of this warp
     for (uint32_t tw = wa; tw < wb; tw += T) {
         const uint32_t k = tw + (uint32_t)(g - gw);
-        compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t0 + k, k < wb, gl, gmask);
+        compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t0 + k, k < wb, search, gl, gmask);
     }
 }
 
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(256) compass_fit_kernel(const FindArgs A) {
 int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int n_events,
                    uint32_t n_tracks, const compass_params* p, compass_tracks* out, int16_t* win, FindArgs& A) {
     if (!ctx || !hits || !velo || !p || !out) return UT_ERR_ARG;
-    if (p->n_sectors < 1 || p->n_sectors > kMaxSectors || p->n_candidates < 1) return UT_ERR_ARG;
+    if (p->n_sectors < 1 || p->n_sectors > kMaxSectors || p->n_candidates < 1 || p->gec_max_hits < 0)
+        return UT_ERR_ARG;
     if (!(p->sigma_hit > 0.f) || !(p->sigma_x_prior > 0.f) || !(p->sigma_tx_prior > 0.f)) return UT_ERR_ARG;
     const ut_geometry& g = ctx->geom;
     A.hx = hits->x;
@@ -120,6 +122,7 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
     A.z_velo = g.z_velo;
     A.n_sec = p->n_sectors;
     A.n_cand = p->n_candidates;
+    A.gec = p->gec_max_hits;
     const float kq = p->kick_k * p->qop_max;
     A.slope_tol = kq + p->tol_slope;
     A.tol_kink = p->tol_kink;

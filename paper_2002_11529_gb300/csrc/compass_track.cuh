@@ -50,6 +50,7 @@ struct FindArgs {
     float inv_pitch;             // 1 / pitch (float estimate of the sector)
     double x_max;                // x_min + S * pitch in double
     int n_sec, n_cand;
+    int gec;                     // Global Event Cut: max UT hits of a searched event (0 = none)
     float slope_tol, tol_kink, tol_col, chi2ndof_max, z_kink;
     float hw[4], t[4], f[4];
     float w, px, ptx;
@@ -566,6 +567,24 @@ __device__ __noinline__ void eval_pair_cold(const FindArgs& A, const View& V, in
     eval_pair<DIR>(A, V, pa, pb, V.d(la, pa), V.d(lb, pb), tk);
 }
 
+// Outputs of a track that is not searched (its event failed the Global
+// Event Cut): no hits, the VELO state, windows (-1, -1).
+template <int G>
+__device__ __forceinline__ void not_searched(const FindArgs& A, uint32_t t, int gl) {
+    if (gl == 0) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
+        A.qop[t] = 0.f;
+        A.chi2[t] = 0.f;
+        A.xo[t] = A.vx[t];
+        A.txo[t] = A.vtx[t];
+        A.nhits[t] = 0;
+        A.found[t] = 0;
+    }
+    if (A.win)
+        for (int j = gl; j < 4 * A.n_sec * 2; j += G) A.win[(size_t)t * 4 * A.n_sec * 2 + j] = -1;
+}
+
 // Setup of VELO track t of event e by its lane group: extrapolation
 // (Sec. V-A), default outputs, the windows and their slot parts.  Returns
 // whether the track is searched (accepted, some window not empty); V gets
@@ -915,15 +934,17 @@ __device__ __forceinline__ void resolve_direction(const FindArgs& A, const View&
 // hits and fit and written.  Every lane of the warp calls this together.
 template <int G>
 __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* ft, PairQueue* Q, const float* X,
-                             const uint32_t* off, uint32_t hb, int e, uint32_t t, bool has_track, int gl,
+                             const uint32_t* off, uint32_t hb, int e, uint32_t t, bool has_track, bool search, int gl,
                              uint32_t gmask) {
     constexpr int T = 32 / G;
     const int lane = threadIdx.x & 31;
     GroupHead* head = wh + lane / G;
-    bool active;
-    {
+    bool active = false;
+    if (has_track && !search) {
+        not_searched<G>(A, t, gl);
+    } else if (has_track) {
         View V0;
-        active = has_track && setup_track<G>(A, head, ft, X, off, e, t, gl, gmask, V0);
+        active = setup_track<G>(A, head, ft, X, off, e, t, gl, gmask, V0);
     }
     if (gl == 0) {
         head->act = active;

@@ -12,6 +12,9 @@ choices for the synthetic detector:
   line's residual at the kink plane within tol_kink.
 * collection: nearest hit within tol_col of the pair line.
 * fit: hit sigma = pitch/sqrt(12), VELO priors sigma_x, sigma_tx.
+* gec_max_hits: the Global Event Cut applied before the tracking (Sec. VI):
+  events with more UT hits are not searched; 0 = no cut.  The paper takes
+  LHCb's cut and gives no value.
 """
 from __future__ import annotations
 
@@ -34,6 +37,7 @@ class CompassParams:
     sigma_tx_prior: float = 1e-5
     z_kink: float = 2500.0
     kick_k: float = 1.2
+    gec_max_hits: int = 0
 
     def replace(self, **kw) -> "CompassParams":
         return dataclasses.replace(self, **kw)

@@ -313,3 +313,24 @@ def test_full_plain_workload_matches_oracle(g):
     gpu = run_compass(g, b, P, form="plain")
     _, orc = oracle.run_batch(b, P)
     assert_tracks_equal(gpu, orc, b)
+
+
+@pytest.mark.parametrize("tpw", [1, 8])
+def test_global_event_cut_matches_oracle(g, tpw):
+    """Events over the Global Event Cut are not searched, in compass_find
+    and in the persistent kernel alike."""
+    b = synth.generate_config("batched", n_events=120)
+    B = b.geom.n_banks
+    ev_hits = b.bank_n.reshape(b.n_events, B).sum(axis=1)
+    params = P.replace(gec_max_hits=int(np.median(ev_hits)))
+    gpu = run_compass(g, b, params, tracks_per_warp=tpw, want_windows=True)
+    _, orc = oracle.run_batch(b, params, want_windows=True)
+    assert_tracks_equal(gpu, orc, b, report=False)
+    assert np.array_equal(gpu["win"], orc.win)
+    ctx = ctx_for(g, b.geom)
+    pipe = g.Pipeline(ctx, b, params)
+    pipe.run_batched(g.LaunchConfig(tracks_per_warp=tpw, block=256))
+    ctx.check(what="batched gec")
+    assert_tracks_equal(g.tracks_to_numpy(pipe.tracks, b.n_tracks), orc, b, report=False)
+    assert int(orc.found.sum()) > 0 and not orc.found[np.repeat(ev_hits > params.gec_max_hits,
+                                                                 np.diff(b.trk_off.astype(np.int64)))].any()

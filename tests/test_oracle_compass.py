@@ -170,3 +170,41 @@ def test_reconstruction_of_generated_tracks_is_reported():
     m = tr.found.astype(bool)
     rel = np.abs(tr.qop64[m] - b.qop_true[m]) / np.abs(b.qop_true[m])
     assert np.median(rel) < 0.05
+
+
+def test_global_event_cut_skips_busy_events_only():
+    """Events with more hits than gec_max_hits are not searched (no found
+    tracks, windows -1); every other event's tracks are those of a run
+    without the cut."""
+    b = synth.generate_config("batched", n_events=30)
+    P = synth.CompassParams()
+    hits, full = oracle.run_batch(b, P, want_windows=True)
+    B = b.geom.n_banks
+    ev_hits = np.diff(hits.hit_off[::B].astype(np.int64))
+    cut = int(np.median(ev_hits))
+    _, gec = oracle.run_batch(b, P.replace(gec_max_hits=cut), want_windows=True)
+    busy = np.repeat(ev_hits > cut, np.diff(b.trk_off.astype(np.int64)))
+    assert busy.any() and (~busy).any()
+    assert not gec.found[busy].any() and np.all(gec.hit[busy] == -1) and np.all(gec.win[busy] == -1)
+    assert np.array_equal(gec.x[busy], b.velo_x[busy]) and np.array_equal(gec.tx[busy], b.velo_tx[busy])
+    for k in ("hit", "found", "nhits", "win"):
+        assert np.array_equal(getattr(gec, k)[~busy], getattr(full, k)[~busy]), k
+    for k in ("qop", "chi2", "x", "tx"):
+        assert np.array_equal(getattr(gec, k)[~busy].view(np.uint32), getattr(full, k)[~busy].view(np.uint32)), k
+
+
+def test_consolidation_keeps_found_tracks_in_order_with_event_offsets():
+    b = synth.generate_config("batched", n_events=25)
+    P = synth.CompassParams()
+    _, tr = oracle.run_batch(b, P)
+    out, off = oracle.consolidate(tr, b.trk_off)
+    found = tr.found.astype(bool)
+    T = b.n_tracks
+    assert off[0] == 0 and off[-1] == found.sum() == out["velo"].size
+    assert np.all(np.diff(out["velo"].astype(np.int64)) > 0) and np.all(found[out["velo"]])
+    for e in range(b.n_events):  # event e's rows hold exactly its found tracks
+        rows = out["velo"][off[e]:off[e + 1]]
+        t0, t1 = int(b.trk_off[e]), int(b.trk_off[e + 1])
+        assert np.array_equal(rows, np.arange(t0, t1)[found[t0:t1]])
+    assert np.array_equal(out["hit"], tr.hit[out["velo"]]) and np.array_equal(out["nhits"], tr.nhits[out["velo"]])
+    assert 0 < found.sum() < T
