@@ -398,6 +398,34 @@ def physics_sweep(g, batch, params, reps=5):
             "reconstructible": ev["reconstructible"], "table": out}
 
 
+def measure_consolidation(g, ctx, pipe, batch, flush, reps=10):
+    """ut_consolidate on the tracks of the last step: device time and the
+    fraction of the measured HBM bandwidth of its algorithmic bytes (found
+    flags and trk_off read, the found tracks' fields read and written)."""
+    import numpy as np
+    import torch
+    E, T = batch.n_events, batch.n_tracks
+    n = int(pipe.tracks.found[:T].sum().item())
+    out = g.CompactTracks.allocate(n)
+    off = torch.empty(E + 1, dtype=torch.int32, device="cuda")
+    ws = g.ut_consolidate(ctx, pipe.velo.trk_off, E, pipe.tracks, out, off)
+    ms = []
+    for _ in range(reps + 1):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.ut_consolidate(ctx, pipe.velo.trk_off, E, pipe.tracks, out, off, ws)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.check(what="consolidation")
+    m = float(np.median(ms[1:]))
+    algo = T + 4 * (E + 1) + n * 33 + n * 37 + 4 * (E + 1)
+    hbm, _ = peaks()
+    return {"found_tracks": n, "ms": m, "algorithmic_bytes": algo, "achieved_gbs": algo / (m / 1e3) / 1e9,
+            "frac": algo / (m / 1e3) / 1e9 / hbm}
+
+
 def e2e_through_server(g, batch, params, cfg, steps, n_slots=4):
     """End to end through the serving engine: every step is one request of
     the whole batch (host inputs in page-locked memory copied in, one
@@ -645,6 +673,7 @@ def main():
         line["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
         line["alignment"] = measure_alignment(g, params)
         line["physics_sweep"] = physics_sweep(g, batch, params)
+        line["consolidation"] = measure_consolidation(g, ctx, pipe, batch, flush)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
     print(json.dumps(line), flush=True)
