@@ -234,7 +234,7 @@ def run_reference(args):
 
 
 def time_forms_on_uneven_workload(g, params, flush, steps=5):
-    """North-star comparison on the 20000-event uneven workload: the batched
+    """Form comparison on the 20000-event uneven workload: the batched
     persistent form (one graph-replayed launch, autotuned shape) against
     the plain per-kernel form (decode, sort, find, fit)."""
     import torch
