@@ -270,7 +270,9 @@ int ut_consolidate(ut_ctx* ctx, const uint32_t* d_trk_off, int n_events, const c
 /* Launch shape of the batched form (0 in a field = its default). */
 typedef struct ut_launch_config {
     int tracks_per_warp;    /* 1, 2, 4 or 8 VELO tracks per warp (default 4)   */
-    int block;              /* 128, 256 or 512 threads per block (default 256) */
+    int block;              /* 128, 256 or 512 threads per block (default 256);
+                               with tracks_per_warp 8 also any multiple of 32
+                               from 544 to 800 (one block per SM) */
     int x_cap;              /* hits of an event kept in shared memory for the
                                search (default 8192, at most 32768; larger
                                events are searched from global memory)       */

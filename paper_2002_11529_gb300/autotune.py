@@ -1,10 +1,13 @@
 """Autotuner for the batched form's launch shape.
 
-Sweeps tracks per warp {1, 2, 4, 8} and block size {128, 256, 512} (the
-per-event shared-memory tile of hit x stays at 8192 hits) on the caller's
-batch (device resident), times each with CUDA events over several passes
-(L2 flushed before each pass), and returns the fastest LaunchConfig with
-the table.
+Sweeps tracks per warp {1, 2, 4, 8} and block size {128, 256, 512}, plus,
+at 8 tracks per warp, large blocks of one per SM: 640, 768, 800 threads and
+the block whose warps cover the batch's median event in one round of warp
+calls (32 x ceil(median tracks / 8) threads, when above 512 and at most
+800).  The per-event shared-memory tile of hit x stays at 8192 hits.  Each
+shape runs on the caller's batch (device resident), timed with CUDA events
+over several passes (L2 flushed before each pass); the fastest
+LaunchConfig is returned with the table.
 Results can be cached in a JSON file keyed by the batch's shape.
 """
 from __future__ import annotations
@@ -21,6 +24,30 @@ from . import LaunchConfig
 TRACKS_PER_WARP = (1, 2, 4, 8)
 BLOCKS = (128, 256, 512)
 X_CAPS = (8192,)
+LARGE_BLOCKS = (640, 768, 800)   # tracks_per_warp 8 only
+LARGE_BLOCK_MAX = 800
+
+
+def round_block(pipe) -> int | None:
+    """Threads of a block whose warps (8 tracks each) cover the median
+    event's tracks in one round, if that is a large block."""
+    per_event = torch.diff(pipe.velo.trk_off.to("cpu", torch.int64))
+    if per_event.numel() == 0:
+        return None
+    med = int(per_event.median())
+    block = 32 * max(1, -(-med // 8))
+    return block if 512 < block <= LARGE_BLOCK_MAX else None
+
+
+def candidates(pipe) -> list:
+    """Launch shapes the autotuner times for this batch."""
+    cfgs = [LaunchConfig(t, b, x) for t, b, x in itertools.product(TRACKS_PER_WARP, BLOCKS, X_CAPS)]
+    large = set(LARGE_BLOCKS)
+    rb = round_block(pipe)
+    if rb is not None:
+        large.add(rb)
+    cfgs += [LaunchConfig(8, b, x) for b in sorted(large) for x in X_CAPS]
+    return cfgs
 
 
 def shape_key(pipe) -> str:
@@ -54,7 +81,7 @@ def autotune(pipe, reps=5, cache_path=None, flush=None, configs=None):
         if key in cache:
             return LaunchConfig(**cache[key]["best"]), [(LaunchConfig(**c), m) for c, m in cache[key]["table"]]
     if configs is None:
-        configs = [LaunchConfig(t, b, x) for t, b, x in itertools.product(TRACKS_PER_WARP, BLOCKS, X_CAPS)]
+        configs = candidates(pipe)
     table = []
     for cfg in configs:
         table.append((cfg, time_config(pipe, cfg, reps, flush)))

@@ -43,8 +43,19 @@ __host__ __device__ inline BatchedLayout batched_layout(int B, uint32_t stage_wo
     return L;
 }
 
+// Large blocks (8 tracks per warp only): any multiple of 32 threads above
+// 512 and up to kLargeBlockMax, one block per SM (72 registers a thread:
+// the register file is handed out to warps in groups of four, and 28 warps
+// x 32 lanes x 72 fit the SM's 65536).  An event's tracks are searched in rounds of one warp call per
+// warp (warps x 8 tracks); a block whose warps cover a typical event's tracks
+// in one round does not pay a second, mostly idle round for the remainder
+// (800 threads: 25 warps x 8 = 200 tracks).
+constexpr int kLargeBlockMax = 800;
+
+// The kernel body.  NT > 0: block of exactly NT threads; NT == 0: block
+// size taken at run time (the large-block kernel).
 template <int G, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeArgs D, const FindArgs A) {
+__device__ __forceinline__ void batched_body(const DecodeArgs& D, const FindArgs& A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ int s_event;
@@ -53,12 +64,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
 
     const int tid = threadIdx.x;
     const int B = 4 * D.S;
-    constexpr int gpb = NT / G;
+    const int nt = NT ? NT : (int)blockDim.x;
+    const int gpb = nt / G;
     const int g = tid / G;
     const int gl = tid % G;
     const int lane = tid & 31;
     const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, gpb, NT / 32);
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, gpb, nt / 32);
     DecodeSmem sm;
     sm.bigcnt = reinterpret_cast<uint32_t*>(smem);
     sm.off = reinterpret_cast<uint32_t*>(smem + L.off_bytes);
@@ -96,7 +108,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
         const float* X = total <= A.x_cap ? sx : D.x + base;
         const bool search = A.gec == 0 || total <= (uint32_t)A.gec;  // Global Event Cut
         // the event's tracks dealt to the warps in equal contiguous shares
-        constexpr int T = 32 / G, W = NT / 32;
+        constexpr int T = 32 / G;
+        const int W = nt / 32;
         const uint32_t t0 = A.trk_off[e], n = A.trk_off[e + 1] - t0;
         const uint32_t q = (n + W - 1) / W, w = (uint32_t)(tid / 32);
         const uint32_t wa = min(n, q * w), wb = min(n, q * (w + 1));
@@ -110,45 +123,68 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
 }
 
 template <int G, int NT>
-static int launch_batched(const DecodeArgs& D, const FindArgs& A, int num_sms, cudaStream_t st) {
+__global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeArgs D, const FindArgs A) {
+    batched_body<G, NT>(D, A);
+}
+
+__global__ void __launch_bounds__(kLargeBlockMax, 1) ut_batched_large_kernel(const DecodeArgs D, const FindArgs A) {
+    batched_body<4, 0>(D, A);
+}
+
+template <int G, int NT>
+static int launch_batched(const DecodeArgs& D, const FindArgs& A, int block, const ut_ctx* ctx, cudaStream_t st) {
     const int B = 4 * D.S;
-    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, NT / G, NT / 32);
+    const int nt = NT ? NT : block;
+    const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, nt / G, nt / 32);
     const size_t smem = L.total;
-    auto kern = ut_batched_kernel<G, NT>;
+    if (smem + 1024 > (size_t)ctx->smem_optin) return UT_ERR_ARG;  // shape does not fit (static smem included)
+    void (*kern)(const DecodeArgs, const FindArgs) = nullptr;
+    if constexpr (NT > 0)
+        kern = ut_batched_kernel<G, NT>;
+    else
+        kern = ut_batched_large_kernel;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
-    // occupancy of this instance, queried once per device and shared-memory
-    // size (so that a later call inside a stream capture makes no query)
+    // occupancy of this instance, queried once per device, shared-memory
+    // size and block (so that a later call inside a stream capture makes no
+    // query)
     static int cached_dev[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     static size_t cached_smem[16];
+    static int cached_nt[16];
     static int cached_per_sm[16];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return UT_ERR_CUDA;
     const int slot = dev & 15;
     int per_sm = 0;
-    if (cached_dev[slot] == dev && cached_smem[slot] == smem) {
+    if (cached_dev[slot] == dev && cached_smem[slot] == smem && cached_nt[slot] == nt) {
         per_sm = cached_per_sm[slot];
     } else {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess || per_sm < 1)
             return UT_ERR_CUDA;
         cached_per_sm[slot] = per_sm;
         cached_smem[slot] = smem;
+        cached_nt[slot] = nt;
         cached_dev[slot] = dev;
     }
-    const long long want = (long long)num_sms * per_sm;
+    const long long want = (long long)ctx->num_sms * per_sm;
     const int grid = (int)(want < D.n_events ? want : D.n_events);
-    kern<<<grid, NT, smem, st>>>(D, A);
+    kern<<<grid, nt, smem, st>>>(D, A);
     return check_cuda(cudaGetLastError());
 }
 
 template <int G>
-static int launch_batched_g(const DecodeArgs& D, const FindArgs& A, int block, int num_sms, cudaStream_t st) {
+static int launch_batched_g(const DecodeArgs& D, const FindArgs& A, int block, const ut_ctx* ctx, cudaStream_t st) {
     switch (block) {
-        case 128: return launch_batched<G, 128>(D, A, num_sms, st);
-        case 256: return launch_batched<G, 256>(D, A, num_sms, st);
-        case 512: return launch_batched<G, 512>(D, A, num_sms, st);
-        default: return UT_ERR_ARG;
+        case 128: return launch_batched<G, 128>(D, A, block, ctx, st);
+        case 256: return launch_batched<G, 256>(D, A, block, ctx, st);
+        case 512: return launch_batched<G, 512>(D, A, block, ctx, st);
+        default: break;
     }
+    if constexpr (G == 4) {
+        if (block > 512 && block <= kLargeBlockMax && block % 32 == 0)
+            return launch_batched<G, 0>(D, A, block, ctx, st);
+    }
+    return UT_ERR_ARG;
 }
 
 }  // namespace utc
@@ -205,10 +241,10 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.vec_ok = hits_aligned16(hits_out);
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
     switch (tpw) {
-        case 1: return launch_batched_g<32>(D, A, block, ctx->num_sms, st);
-        case 2: return launch_batched_g<16>(D, A, block, ctx->num_sms, st);
-        case 4: return launch_batched_g<8>(D, A, block, ctx->num_sms, st);
-        case 8: return launch_batched_g<4>(D, A, block, ctx->num_sms, st);
+        case 1: return launch_batched_g<32>(D, A, block, ctx, st);
+        case 2: return launch_batched_g<16>(D, A, block, ctx, st);
+        case 4: return launch_batched_g<8>(D, A, block, ctx, st);
+        case 8: return launch_batched_g<4>(D, A, block, ctx, st);
         default: return UT_ERR_ARG;
     }
 }

@@ -122,6 +122,7 @@ struct ut_ctx {
     unsigned long long* h_status;  // pinned
     int device;
     int num_sms;
+    int smem_optin;  // largest dynamic shared memory a block may opt in to
 };
 
 namespace utc {

@@ -17,6 +17,7 @@ extern "C" int ut_ctx_create(ut_ctx** out, const ut_geometry* geom) {
     c->geom = g;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess ||
         cudaMalloc(&c->d_status, sizeof(unsigned long long)) != cudaSuccess) {
         delete c;
         return UT_ERR_CUDA;

@@ -15,7 +15,7 @@
 
 namespace utc {
 
-constexpr int kMaxDecodeThreads = 512;
+constexpr int kMaxDecodeThreads = 1024;
 constexpr int kSmallBank = 64;          // banks up to this size rank by direct counting
 constexpr int kBigWarps = 1;            // warps that sort larger banks
 constexpr int kKeyBins = 1024;          // half-strip keys (strips <= 512)

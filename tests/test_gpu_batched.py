@@ -56,6 +56,38 @@ def test_batched_launch_shapes(g, tpw, block):
     check_against_oracle(g, pipe, b)
 
 
+@pytest.mark.parametrize("block", [544, 672, 800])
+def test_batched_large_blocks(g, block):
+    """One block per SM of up to 25 warps (8 tracks per warp), on uneven
+    events (many need several rounds of warp calls) and on events of 200
+    tracks (one round at 800 threads)."""
+    for b in (synth.generate_config("batched", n_events=60, seed=37),
+              synth.generate_config("plain", n_events=64)):
+        ctx = g.Context(b.geom)
+        pipe = g.Pipeline(ctx, b, P)
+        pipe.run_batched(g.LaunchConfig(8, block, 8192, 8192))
+        ctx.check(what="batched")
+        check_against_oracle(g, pipe, b)
+        ctx.close()
+
+
+@pytest.mark.parametrize("tpw,block,x_cap", [(4, 800, 8192), (8, 816, 8192), (8, 600, 8192),
+                                             (8, 1024, 8192), (8, 800, 32768)])
+def test_batched_rejects_unsupported_shapes(g, tpw, block, x_cap):
+    """Large blocks exist for 8 tracks per warp only, as multiples of 32 up
+    to 800 threads, and the shape must fit the block's shared memory: the
+    call returns UT_ERR_ARG before any launch."""
+    b = synth.generate_config("tiny")
+    ctx = g.Context(b.geom)
+    pipe = g.Pipeline(ctx, b, P)
+    with pytest.raises(g.UtError) as err:
+        pipe.run_batched(g.LaunchConfig(tpw, block, x_cap, 8192))
+    assert err.value.code == g.UT_ERR_ARG
+    pipe.run_batched(g.LaunchConfig(8, 800, 8192, 8192))  # the context stays usable
+    ctx.check(what="batched")
+    check_against_oracle(g, pipe, b)
+
+
 @pytest.mark.parametrize("x_cap,stage", [(256, 8192), (8192, 64), (0, 0)])
 def test_batched_global_fallbacks(g, x_cap, stage):
     """Events larger than the shared-memory tiles are read from global memory."""
@@ -113,9 +145,10 @@ def test_autotuner_picks_a_valid_config(g):
     ctx = g.Context(b.geom)
     pipe = g.Pipeline(ctx, b, P)
     best, table = autotune.autotune(pipe, reps=1)
-    n_shapes = len(autotune.TRACKS_PER_WARP) * len(autotune.BLOCKS) * len(autotune.X_CAPS)
-    assert len(table) == n_shapes and all(ms > 0 for _, ms in table)
-    assert {c.block for c, _ in table} == {128, 256, 512} and best in [c for c, _ in table]
+    n_small = len(autotune.TRACKS_PER_WARP) * len(autotune.BLOCKS) * len(autotune.X_CAPS)
+    assert len(table) == len(autotune.candidates(pipe)) >= n_small + len(autotune.LARGE_BLOCKS)
+    assert all(ms > 0 for _, ms in table) and best in [c for c, _ in table]
+    assert {128, 256, 512, *autotune.LARGE_BLOCKS} <= {c.block for c, _ in table}
     pipe.run_batched(best)
     ctx.check(what="autotuned")
     check_against_oracle(g, pipe, b)
@@ -134,3 +167,36 @@ def test_full_batched_workload_matches_oracle(g):
     print(f"\n20000 events: {b.n_tracks} tracks, found {int(m.sum())}, near-cut {int((ot.near <= 1e-5).sum())}, "
           f"float q/p vs double: max rel {rel.max():.2e}")
     assert rel.max() <= 1e-5
+
+
+def test_full_plain_workload_every_tuned_shape(g):
+    """The 1000-event, 256-sector workload in the benchmark's default launch:
+    the persistent kernel captured in a CUDA graph and replayed, for every
+    launch shape the autotuner can pick, each compared with the oracle."""
+    from paper_2002_11529_gb300 import autotune
+    b = synth.generate_config("plain")
+    oh, ot = oracle.run_batch(b, P)
+    ctx = g.Context(b.geom)
+    pipe = g.Pipeline(ctx, b, P)
+    shapes = autotune.candidates(pipe)
+    assert g.LaunchConfig(8, 800) in shapes      # 200 tracks per event: one round of 25 warps
+    for cfg in shapes:
+        t, blk = cfg.tracks_per_warp, cfg.block
+        runner = g.GraphRunner(pipe, cfg)
+        for _ in range(2):
+            pipe.tracks.qop.fill_(123.0)
+            pipe.tracks.hit.fill_(-7)
+            pipe.hits_a.x.fill_(-1.0)
+            runner.replay()
+            torch.cuda.synchronize()
+            ctx.check(what=f"graph tpw={t} block={blk}")
+        hits = g.hits_to_numpy(pipe.hits_a)
+        tr = g.tracks_to_numpy(pipe.tracks, b.n_tracks)
+        assert np.array_equal(hits["hit_off"], oh.hit_off)
+        assert np.array_equal(hits["x"][:oh.n].view(np.uint32), oh.x.view(np.uint32))
+        assert np.array_equal(hits["id"][:oh.n], oh.id)
+        assert np.array_equal(tr["hit"], ot.hit), (t, blk)
+        assert np.array_equal(tr["found"], ot.found) and np.array_equal(tr["nhits"], ot.nhits)
+        for k in ("qop", "chi2", "x", "tx"):
+            assert np.array_equal(tr[k].view(np.uint32), getattr(ot, k).view(np.uint32)), (k, t, blk)
+    ctx.close()
