@@ -281,8 +281,9 @@ def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95)):
     """Serving: requests of 64-4096 events (log-uniform, plain-workload
     occupancy) through the continuous-batching engine, 40 GB budget,
     8 stream slots, persistent launch shape `cfg`: sustained peak (all
-    submitted at once), then Poisson arrivals at fractions of that peak;
-    p50/p99 request latency."""
+    submitted at once), then Poisson arrivals at fractions of that peak
+    (96 requests per level, after an untimed open-loop pass); p50/p99
+    request latency."""
     import numpy as np
     import synth
     from paper_2002_11529_gb300 import serve
@@ -291,16 +292,17 @@ def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95)):
     batches = [synth.generate(n_events=int(n), n_sectors=256, tracks=200, hits=4000, seed=7000 + i)
                for i, n in enumerate(sizes)]
     reqs = [serve.HostRequest.from_batch(b) for b in batches]
-    res = {"requests_per_level": 2 * len(reqs), "events_per_request": "64-4096 log-uniform",
+    res = {"requests_per_level": 4 * len(reqs), "events_per_request": "64-4096 log-uniform",
            "budget_bytes": 40 << 30, "slots": 8,
            "launch": None if cfg is None else {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block}}
     with serve.Server(batches[0].geom, params, budget_bytes=40 << 30, n_slots=8, cfg=cfg) as sv:
         serve.run_closed_loop(sv, reqs)            # warm-up
-        peak, _ = serve.run_closed_loop(sv, reqs + reqs)
+        peak, _ = serve.run_closed_loop(sv, reqs * 4)
         res["peak_events_per_s"] = peak["events_per_s"]
         res["peak_p99_ms"] = peak["p99_ms"]
+        serve.run_open_loop(sv, reqs, events_per_s=0.5 * peak["events_per_s"], seed=1)  # warm-up
         for f in loads:
-            summ, _ = serve.run_open_loop(sv, reqs + reqs, events_per_s=f * peak["events_per_s"], seed=int(f * 100))
+            summ, _ = serve.run_open_loop(sv, reqs * 4, events_per_s=f * peak["events_per_s"], seed=int(f * 100))
             res[f"load_{int(round(f * 100))}"] = {k: summ[k] for k in ("events_per_s", "p50_ms", "p99_ms",
                                                                        "queue_p50_ms", "errors")}
         res["arena_peak_bytes"] = sv.stats()["arena_peak"]
