@@ -302,9 +302,11 @@ __device__ __forceinline__ DecodedHit decoded_hit(const DecodeArgs& a, int b, ui
 // hit is the number of keys of its bank below its own, kept in bits 10-15
 // of bmap[i].  Then srcmap[off[b] + r] = position of the hit's word in the
 // event's 16-bit words.  The key array occupies srcmap until the ranks are
-// taken.  Larger banks are ranked by rank_big_banks straight into srcmap.
+// taken.  Larger banks (any_big: the event has some) are ranked by
+// rank_big_banks straight into srcmap.
 template <bool SORT>
-__device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total) {
+__device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total,
+                          bool any_big) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int B = 4 * a.S;
     const uint32_t* off = sm.off;
@@ -345,9 +347,10 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
             for (; j < n; ++j) r += (uint32_t)(K[j] < key);
             bmap[i] = (uint16_t)(b | (r << 10));
         }
-        rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
-            srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
-        });
+        if (any_big)
+            rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
+                srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
+            });
         __syncthreads();
         for (uint32_t i = tid; i < total; i += nt) {
             const uint32_t v = bmap[i];
@@ -460,6 +463,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     }
 
     // Hit counting with directory / header checks (one thread per bank).
+    bool big = false;  // a bank of more than kSmallBank hits (ranked by rank_big_banks)
     for (int b = tid; b < B; b += nt) {
         uint32_t n = 0;
         if (ev_ok) {
@@ -479,8 +483,9 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
             }
         }
         off[b] = n;
+        big |= n > (uint32_t)kSmallBank;
     }
-    __syncthreads();
+    const bool any_big = __syncthreads_or(big) != 0;
     const uint32_t total = block_exclusive_scan(off, B, sm.warp_tot);
 
     // Publish the aggregate at once; look back only after the event's own
@@ -490,7 +495,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
         st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
     // (sorted: bank and rank share 16 bits, word positions fit 16 bits)
     const bool mapped = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
-    if (mapped) map_event<SORT>(a, sm, evw, total);
+    if (mapped) map_event<SORT>(a, sm, evw, total, any_big);
     if (tid < 32) {
         const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
         if (tid == 0) {
@@ -534,7 +539,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
             write_hit(a, (uint32_t)(base + off[b] + r), l, s, w, sx, sx_cap, off[b] + r);
         }
     }
-    if (SORT && fits)
+    if (SORT && fits && any_big)
         rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t, uint32_t w) {
             int l, s;
             bank_ls(b, S, l, s);
