@@ -47,7 +47,9 @@ class _Params(ctypes.Structure):
     _fields_ = [("n_sectors", ctypes.c_int), ("n_candidates", ctypes.c_int)] + [
         (n, ctypes.c_float) for n in ("qop_max", "tol_win", "tol_kink", "tol_col", "tol_slope",
                                       "chi2ndof_max", "sigma_hit", "sigma_x_prior",
-                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int)]
+                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int)] + [
+        ("kmap_nx", ctypes.c_int), ("kmap_ny", ctypes.c_int), ("kmap_tx_max", ctypes.c_float),
+        ("kmap_ty_max", ctypes.c_float), ("kmap_v", ctypes.c_void_p)]
 
 
 def lib():
@@ -75,6 +77,8 @@ def lib():
             _lib.orc_fit32_d.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, P]
             _lib.orc_max_threads.restype = ctypes.c_int
+            _lib.orc_kick_at.restype = ctypes.c_float
+            _lib.orc_kick_at.argtypes = [P, ctypes.c_float, ctypes.c_float]
             _lib.orc_align_chi2.restype = ctypes.c_int
             _lib.orc_align_chi2.argtypes = [P, P, P, P, ctypes.c_uint32, P, P, P, P, P, P, P, P,
                                             P, P, P, P]
@@ -124,11 +128,29 @@ def geom_struct(geom) -> _Geom:
     return g
 
 
-def params_struct(p) -> _Params:
+def params_struct(p, kick_map=None) -> _Params:
+    """kick_map: None (the constant kick_k) or an object with nx, ny, tx_max,
+    ty_max and values (float32 [ny, nx]) -- the field map of Sec. III-C."""
     s = _Params()
     for f in dataclasses.fields(p):
         setattr(s, f.name, getattr(p, f.name))
+    if kick_map is not None:
+        v = np.ascontiguousarray(kick_map.values, np.float32)
+        assert v.shape == (kick_map.ny, kick_map.nx)
+        s.kmap_nx, s.kmap_ny = int(kick_map.nx), int(kick_map.ny)
+        s.kmap_tx_max, s.kmap_ty_max = float(kick_map.tx_max), float(kick_map.ty_max)
+        s.kmap_v = v.ctypes.data
+        s._keep = v  # the values must outlive the call
     return s
+
+
+def kick_at(params, kick_map, tx, ty):
+    """The kick map evaluated at track directions (tx, ty) (float32 arrays)."""
+    pp = params_struct(params, kick_map)
+    tx = np.asarray(tx, np.float32).ravel()
+    ty = np.asarray(ty, np.float32).ravel()
+    return np.array([lib().orc_kick_at(ctypes.byref(pp), ctypes.c_float(a), ctypes.c_float(b))
+                     for a, b in zip(tx, ty)], np.float32)
 
 
 def decode(raw, ev_off, n_events, geom, sorted_=True, capacity=None, n_threads=0,
@@ -189,10 +211,11 @@ class Tracks:
 
 
 def compass(hx, hit_off, n_events, geom, velo, params, want_windows=False, n_threads=0,
-            raise_on_error=True):
+            raise_on_error=True, kick_map=None):
     """Windows + tracklet search + selection (Sec. V) for every VELO track.
 
     velo: object with x, y, tx, ty (f32), flags (u8), trk_off (u32[E+1]).
+    kick_map: see params_struct.
     """
     hx = np.ascontiguousarray(hx, dtype=np.float32)
     hit_off = np.ascontiguousarray(hit_off, dtype=np.uint32)
@@ -210,7 +233,7 @@ def compass(hx, hit_off, n_events, geom, velo, params, want_windows=False, n_thr
                  np.full((Tn, 4, params.n_sectors, 2), -1, np.int16) if want_windows else None,
                  np.zeros(Tn, np.float64), np.zeros(Tn, np.float64), np.zeros(Tn, np.float64))
     g = geom_struct(geom)
-    pp = params_struct(params)
+    pp = params_struct(params, kick_map)
     et = np.zeros(1, np.int64)
     rc = lib().orc_compass(_p(hx), _p(hit_off), n_events, ctypes.byref(g), _p(vx), _p(vy), _p(vtx),
                            _p(vty), _p(vfl), _p(toff), ctypes.byref(pp), _p(out.hit), _p(out.qop),
@@ -224,7 +247,7 @@ def compass(hx, hit_off, n_events, geom, velo, params, want_windows=False, n_thr
     return out
 
 
-def fit_tracks(hx, geom, velo, hit, params):
+def fit_tracks(hx, geom, velo, hit, params, kick_map=None):
     """Refit given hit sets (float and double).  Returns dict of arrays."""
     hx = np.ascontiguousarray(hx, dtype=np.float32)
     hit = np.ascontiguousarray(hit, dtype=np.int32)
@@ -238,7 +261,7 @@ def fit_tracks(hx, geom, velo, hit, params):
     o["qop64"] = np.zeros(max(T, 1), np.float64)
     o["chi2_64"] = np.zeros(max(T, 1), np.float64)
     g = geom_struct(geom)
-    pp = params_struct(params)
+    pp = params_struct(params, kick_map)
     lib().orc_fit_tracks(_p(hx), ctypes.byref(g), _p(vx), _p(vy), _p(vtx), _p(vty), T, _p(hit),
                          ctypes.byref(pp), _p(o["qop"]), _p(o["chi2"]), _p(o["x"]), _p(o["tx"]),
                          _p(o["ok"]), _p(o["qop64"]), _p(o["chi2_64"]))
@@ -278,11 +301,11 @@ class Velo:
         self.trk_off = batch.trk_off
 
 
-def run_batch(batch, params, n_threads=0, want_windows=False):
+def run_batch(batch, params, n_threads=0, want_windows=False, kick_map=None):
     """Decode (sorted) + Compass for a whole batch: (Hits, Tracks)."""
     _, hits, _ = decode(batch.raw, batch.ev_off, batch.n_events, batch.geom, True, n_threads=n_threads)
     tr = compass(hits.x, hits.hit_off, batch.n_events, batch.geom, Velo(batch), params,
-                 want_windows=want_windows, n_threads=n_threads)
+                 want_windows=want_windows, n_threads=n_threads, kick_map=kick_map)
     return hits, tr
 
 

@@ -22,7 +22,9 @@
  *   Sec. V-B       tracklet finding: anchors in panels 1 and 3, tolerance in
  *                  2 and 4, >= 3 hits, forward then backward, combined range
  *                  order, candidate count, chi2 selection
- *   Sec. III-C     p-kick chi2 fit instead of a Kalman filter
+ *   Sec. III-C     p-kick chi2 fit instead of a Kalman filter; look-up
+ *                  tables for the magnetic field: a kick map K(tx, ty)
+ *                  (kick_at) in place of the constant kick
  *   Sec. V-C       CPU form: windows computed per track right before the
  *                  tracklet search, OpenMP over events
  *
@@ -259,12 +261,48 @@ typedef struct {
     float qop_max, tol_win, tol_kink, tol_col, tol_slope, chi2ndof_max;
     float sigma_hit, sigma_x_prior, sigma_tx_prior, z_kink, kick_k;
     int gec_max_hits; /* Global Event Cut (Sec. VI): events with more hits are not searched */
+    /* Kick map (Sec. III-C: look-up tables give the deflection a track is
+     * expected to get).  kmap_nx = 0: the constant kick_k.  Else K(tx, ty) on
+     * an nx x ny grid over tx in [-kmap_tx_max, kmap_tx_max], ty in
+     * [-kmap_ty_max, kmap_ty_max], values kmap_v[iy * nx + ix]. */
+    int kmap_nx, kmap_ny;
+    float kmap_tx_max, kmap_ty_max;
+    const float* kmap_v;
 } orc_params;
 
 typedef struct {
     int S;
     float z[4], tan_a[4], pitch, x_min, z_velo;
 } orc_geom;
+
+/*
+ * The kick of a track of direction (tx, ty): bilinear interpolation of the
+ * map, the coordinates clamped to the grid.  Cell i spans grid coordinate
+ * [i, i + 1]; the coordinate of tx is (tx + tx_max) * (nx - 1) / (2 tx_max).
+ * Float, every operation in the order written.
+ */
+static float kick_at(const orc_params* p, float tx, float ty) {
+    const int nx = p->kmap_nx, ny = p->kmap_ny;
+    const float sx = (float)(nx - 1) / (2.0f * p->kmap_tx_max);
+    const float sy = (float)(ny - 1) / (2.0f * p->kmap_ty_max);
+    float fx = (tx + p->kmap_tx_max) * sx;
+    float fy = (ty + p->kmap_ty_max) * sy;
+    fx = fminf(fmaxf(fx, 0.0f), (float)(nx - 1));
+    fy = fminf(fmaxf(fy, 0.0f), (float)(ny - 1));
+    int ix = (int)fx, iy = (int)fy;
+    if (ix > nx - 2) ix = nx - 2;
+    if (iy > ny - 2) iy = ny - 2;
+    const float ax = fx - (float)ix, ay = fy - (float)iy;
+    const float* v = p->kmap_v;
+    const float v00 = v[iy * nx + ix], v01 = v[iy * nx + ix + 1];
+    const float v10 = v[(iy + 1) * nx + ix], v11 = v[(iy + 1) * nx + ix + 1];
+    const float r0 = v00 + ax * (v01 - v00);
+    const float r1 = v10 + ax * (v11 - v10);
+    return r0 + ay * (r1 - r0);
+}
+
+/* The kick map evaluated on its own (exposed for tests). */
+float orc_kick_at(const orc_params* p, float tx, float ty) { return kick_at(p, tx, ty); }
 
 /* Relative margin of a decision a <op> b. */
 static double margin(double a, double b) {
@@ -443,6 +481,9 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
     const int S = g->S, B = 4 * S;
     const int nsec = p->n_sectors;
     if (nsec < 1 || nsec > 5 || p->n_candidates < 1 || p->gec_max_hits < 0) return ORC_ERR_ARG;
+    if (p->kmap_nx != 0 && (p->kmap_nx < 2 || p->kmap_ny < 2 || !p->kmap_v || !(p->kmap_tx_max > 0.f) ||
+                            !(p->kmap_ty_max > 0.f)))
+        return ORC_ERR_ARG;
     static const int slot_off[5] = {0, -1, 1, -2, 2};
     const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
     const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
@@ -485,6 +526,19 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             if (m1 < mm) mm = m1;
             if (!(u[0] >= (double)g->x_min && u[0] <= x_max)) { near_m[tr] = mm; continue; }
 
+            /* The track's kick: the map's K(tx, ty), else the constant.  It
+             * sets the window half-widths and the slope cut (the largest
+             * deflection of a track of this direction at qop_max), and
+             * converts the fitted kick coefficient into q/p below. */
+            float hwt[4], stol = slope_tol, kick = p->kick_k;
+            for (int l = 0; l < 4; ++l) hwt[l] = hw[l];
+            if (p->kmap_nx) {
+                kick = kick_at(p, vtx[tr], vty[tr]);
+                const float kqt = kick * p->qop_max;
+                for (int l = 0; l < 4; ++l) hwt[l] = kqt * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+                stol = kqt + p->tol_slope;
+            }
+
             /* Windows (Sec. V-A): central sector, then neighbours. */
             int any = 0;
             for (int l = 0; l < 4; ++l) {
@@ -504,10 +558,10 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
                     int64_t first = -1, last = -1;
                     for (uint32_t j = a; j < bnd; ++j) {
                         float dj = (hx[j] - uhi[l]) - ulo[l];
-                        double ma = margin(dj, -hw[l]), mb = margin(dj, hw[l]);
+                        double ma = margin(dj, -hwt[l]), mb = margin(dj, hwt[l]);
                         if (ma < mm) mm = ma;
                         if (mb < mm) mm = mb;
-                        if (dj >= -hw[l] && dj <= hw[l]) {
+                        if (dj >= -hwt[l] && dj <= hwt[l]) {
                             if (first < 0) first = j;
                             last = j;
                         }
@@ -555,9 +609,9 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
                         const float db = dv[lb][ib];
                         const float sr = (db - da) / dzab;
                         double m;
-                        m = margin(fabsf(sr), slope_tol);
+                        m = margin(fabsf(sr), stol);
                         if (m < mm) mm = m;
-                        if (!(fabsf(sr) <= slope_tol)) continue;
+                        if (!(fabsf(sr) <= stol)) continue;
                         const float dk = da + sr * dzk;
                         m = margin(fabsf(dk), p->tol_kink);
                         if (m < mm) mm = m;
@@ -613,7 +667,10 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             near_m[tr] = mm;
             if (best_n == 0) continue;
             for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = best_hit[l];
-            qop[tr] = best_q;
+            /* The fit's kick coefficient is q/p in units of the constant kick;
+             * with the map, q/p = coefficient * kick_k / K (the chi2, x and tx
+             * do not depend on the scale of the kick column). */
+            qop[tr] = p->kmap_nx ? best_q * (p->kick_k / kick) : best_q;
             chi2[tr] = best_chi2;
             xo[tr] = vx[tr] + best_a;
             txo[tr] = vtx[tr] + best_b;
@@ -630,7 +687,7 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             }
             double sh = (double)p->sigma_hit, sx = (double)p->sigma_x_prior, st = (double)p->sigma_tx_prior;
             if (orc_fit64_d(d64, pr, t64, f64, 1.0 / (sh * sh), 1.0 / (sx * sx), 1.0 / (st * st), delta, &c64)) {
-                qop64[tr] = delta[2];
+                qop64[tr] = p->kmap_nx ? delta[2] * ((double)p->kick_k / (double)kick) : delta[2];
                 chi2_64[tr] = c64;
             }
         }
@@ -682,13 +739,15 @@ int orc_fit_tracks(const float* hx, const orc_geom* g, const float* vx, const fl
         qop[tr] = 0.f; chi2[tr] = 0.f; xo[tr] = vx[tr]; txo[tr] = vtx[tr]; ok[tr] = 0;
         qop64[tr] = 0.0; chi2_64[tr] = 0.0;
         if (n < 3) continue;
+        const float kick = p->kmap_nx ? kick_at(p, vtx[tr], vty[tr]) : p->kick_k;
         float a, b, q, c2;
         if (fit32(d, pr, t, f, w, px, ptx, &a, &b, &q, &c2)) {
-            qop[tr] = q; chi2[tr] = c2; xo[tr] = vx[tr] + a; txo[tr] = vtx[tr] + b; ok[tr] = 1;
+            qop[tr] = p->kmap_nx ? q * (p->kick_k / kick) : q;
+            chi2[tr] = c2; xo[tr] = vx[tr] + a; txo[tr] = vtx[tr] + b; ok[tr] = 1;
         }
         double delta[3], c64;
         if (orc_fit64_d(d64, pr, t64, f64, 1.0 / (sh * sh), 1.0 / (sx * sx), 1.0 / (st * st), delta, &c64)) {
-            qop64[tr] = delta[2];
+            qop64[tr] = p->kmap_nx ? delta[2] * ((double)p->kick_k / (double)kick) : delta[2];
             chi2_64[tr] = c64;
         }
     }

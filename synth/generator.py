@@ -18,7 +18,10 @@ neither):
 Trajectories (the magnet kick as a kink, Sec. III-C): a VELO track is a
 straight line given at z = 770 mm by (x, y, tx, ty); in the UT the true
 position is x(z) = x + tx*(z-770) + 1.2*qop*(z-2500), y(z) = y + ty*(z-770),
-with qop = charge/p in 1/GeV.
+with qop = charge/p in 1/GeV.  With `field_fn` (the "fieldmap" workload)
+the kick 1.2 is replaced by field_fn(tx, ty), a direction-dependent field
+integral (`field_kick`); the tracking is given that field only as a map
+sampled on a grid (`kick_map`), as the paper's look-up tables.
 
 Raw bank layout (the paper calls it a "highly compact format" without a bit
 layout; this layout is this project's):
@@ -49,6 +52,37 @@ N_STRIPS = 512
 Z_VELO = 770.0
 Z_KINK = 2500.0
 KICK_K = 1.2           # mm of x per mm of z per GeV^-1 (1.2e3 mm*GeV/1000)
+
+
+def field_kick(tx, ty) -> np.ndarray:
+    """Kick of the synthetic magnet per unit q/p (mm of x per mm of z per
+    GeV^-1) for a track of direction (tx, ty): KICK_K scaled by a smooth
+    field integral, larger for tracks at large |ty| and smaller at large |tx|
+    (up to +40 % and -20 % over the VELO acceptance).  A property of the
+    simulated detector; the tracking only sees it sampled by `kick_map`."""
+    tx = np.asarray(tx, np.float64)
+    ty = np.asarray(ty, np.float64)
+    return KICK_K * (1.0 + 0.4 * (ty / 0.25) ** 2) * (1.0 - 0.2 * (tx / 0.3) ** 2)
+
+
+@dataclasses.dataclass
+class KickMap:
+    """A field map of the kick: values[j, i] is the kick at tx_i = -tx_max +
+    i * 2 tx_max / (nx - 1), ty_j = -ty_max + j * 2 ty_max / (ny - 1)."""
+    nx: int
+    ny: int
+    tx_max: float
+    ty_max: float
+    values: np.ndarray  # float32 [ny, nx]
+
+
+def kick_map(nx: int = 17, ny: int = 17, tx_max: float = 0.3, ty_max: float = 0.25, fn=None) -> KickMap:
+    """`fn` (default field_kick) sampled on the grid, rounded to float32."""
+    fn = field_kick if fn is None else fn
+    tx = -tx_max + np.arange(nx, dtype=np.float64) * (2.0 * tx_max / (nx - 1))
+    ty = -ty_max + np.arange(ny, dtype=np.float64) * (2.0 * ty_max / (ny - 1))
+    v = fn(tx[None, :], ty[:, None]).astype(np.float32)
+    return KickMap(nx, ny, tx_max, ty_max, np.ascontiguousarray(v))
 
 
 def tan_stereo_f32() -> np.ndarray:
@@ -123,6 +157,8 @@ CONFIGS = {
     "tiny": dict(n_events=16, n_sectors=64, tracks=100, hits=1500, seed=1),
     "plain": dict(n_events=1000, n_sectors=256, tracks=200, hits=4000, seed=2),
     "batched": dict(n_events=20000, n_sectors=256, tracks=None, hits="lognormal", seed=3),
+    # the plain workload's shapes, hits made with the direction-dependent field
+    "fieldmap": dict(n_events=1000, n_sectors=256, tracks=200, hits=4000, seed=6, field_fn=field_kick),
 }
 
 
@@ -142,7 +178,7 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
              noise_frac: float | None = None, efficiency: float = 0.95,
              backward_frac: float = 0.0, field: float = KICK_K,
              smear: bool = True, plane_covering: bool = False,
-             p_range=(1.5, 100.0), flags_random: bool = True, misalign=None) -> Batch:
+             p_range=(1.5, 100.0), flags_random: bool = True, misalign=None, field_fn=None) -> Batch:
     """Generate a seeded batch.
 
     hits: target hits per event (noise = target - signal, at least 0), or
@@ -150,6 +186,7 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
     tracks = round(0.05*hits)), or None together with noise_frac (noise hits
     = noise_frac/(1-noise_frac) * signal hits).
     field: kick constant used to make the hits (0 gives straight tracks).
+    field_fn: optional f(tx, ty) -> kick per track (float64), replacing field.
     plane_covering: VELO x at z=770 drawn so that the tracks cover the plane
     (used by the alignment workload) instead of coming from the beam line.
     misalign: optional (dx, dz, gamma), each [4, S]: sector (l, s) sits at
@@ -189,6 +226,8 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
     vtx = tx.astype(np.float32)
     vty = ty.astype(np.float32)
     qop32 = qop.astype(np.float32)
+    kick = (np.full(T, float(field)) if field_fn is None
+            else np.asarray(field_fn(vtx.astype(np.float64), vty.astype(np.float64)), np.float64))
 
     z = np.asarray(Z_LAYERS, dtype=np.float64)
     tan_a = tan_stereo_f32().astype(np.float64)
@@ -205,7 +244,7 @@ def generate(n_events: int, n_sectors: int, tracks=100, hits=1500, seed: int = 1
     flag_v = rng.integers(0, 32, 4 * T) if flags_random else np.zeros(4 * T, np.int64)
     def measure(zz, dxs, gam):
         dz = zz - Z_VELO
-        xt = vx[tl_t].astype(np.float64) + vtx[tl_t] * dz + field * qop32[tl_t].astype(np.float64) * (zz - Z_KINK)
+        xt = vx[tl_t].astype(np.float64) + vtx[tl_t] * dz + kick[tl_t] * qop32[tl_t].astype(np.float64) * (zz - Z_KINK)
         yt = vy[tl_t].astype(np.float64) + vty[tl_t] * dz
         ta = (tan_a[tl_l] + np.tan(gam)) / (1.0 - tan_a[tl_l] * np.tan(gam))
         return xt - dxs - yt * ta + smear_v
