@@ -400,6 +400,51 @@ def physics_sweep(g, batch, params, reps=5):
             "reconstructible": ev["reconstructible"], "table": out}
 
 
+def measure_kick_map(g, params, cfg, reps=10):
+    """The field look-up table of the kick (row f4) on the fieldmap workload
+    (the plain workload's shapes, hits made with a direction-dependent
+    field): the persistent form's events/s (graph replay, L2 flushed) with
+    the field's 17 x 17 map and with the constant kick, and for each the
+    efficiency, fake rate and the median |q/p / true q/p - 1| of the
+    found 4-hit tracks of the particles they were made from."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2002_11529_gb300 import physics
+    b = synth.generate_config("fieldmap")
+    ctx = g.Context(b.geom)
+    pipe = g.Pipeline(ctx, b, params)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    truth = b.qop_true.astype(np.float64)
+    res = {"workload": "fieldmap: 1000 events, 4x256 sectors, hits/event 4000, tracks/event 200, "
+                       "kick = field_kick(tx, ty) (KICK_K x [0.8, 1.4])",
+           "launch": {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block}}
+    for name, km in (("map_17x17", synth.kick_map()), ("constant_kick", None)):
+        ctx.set_kick_map(km)
+        runner = g.GraphRunner(pipe, cfg)
+        ms = []
+        for r in range(reps + 1):
+            flush.add_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            runner.replay()
+            e1.record()
+            e1.synchronize()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+        ctx.check(what="kick map")
+        tr = g.tracks_to_numpy(pipe.tracks, b.n_tracks)
+        ev = physics.evaluate(b, tr)
+        own = physics.own_track(b, tr)
+        sel = (tr["nhits"] == 4) & own
+        res[name] = {"events_per_s": b.n_events / float(np.median(ms)) * 1e3,
+                     "efficiency": ev["efficiency"], "fake_rate": ev["fake_rate"],
+                     "qop_median_rel_err": float(np.median(np.abs(tr["qop"][sel] / truth[sel] - 1.0)))}
+        del runner
+    ctx.close()
+    return res
+
+
 def measure_consolidation(g, ctx, pipe, batch, flush, reps=10):
     """ut_consolidate on the tracks of the last step: device time and the
     fraction of the measured HBM bandwidth of its algorithmic bytes (found
@@ -675,6 +720,7 @@ def main():
         line["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
         line["alignment"] = measure_alignment(g, params)
         line["physics_sweep"] = physics_sweep(g, batch, params)
+        line["kick_map"] = measure_kick_map(g, params, cfg if args.form == "batched" else g.LaunchConfig(8, 512))
         line["consolidation"] = measure_consolidation(g, ctx, pipe, batch, flush)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)

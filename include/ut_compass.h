@@ -127,6 +127,32 @@ typedef struct ut_ctx ut_ctx;
 int ut_ctx_create(ut_ctx** ctx, const ut_geometry* geom);
 int ut_ctx_destroy(ut_ctx* ctx);
 
+/*
+ * ut_ctx_set_kick_map -- field look-up table for the kick (Sec. III-C:
+ * look-up tables give the deflection a track is expected to get).  The
+ * kick of a VELO track of direction (tx, ty) becomes K(tx, ty), the
+ * bilinear interpolation of host_values[iy * nx + ix] (row-major, float)
+ * on the grid tx_ix = -tx_max + ix * 2 tx_max / (nx - 1), ty_iy likewise,
+ * the coordinates clamped to the grid; in float, each operation in this
+ * order: sx = (nx - 1) / (2 tx_max), fx = clamp((tx + tx_max) * sx, 0,
+ * nx - 1), ix = min(int(fx), nx - 2), ax = fx - ix (same for y),
+ * r0 = v00 + ax (v01 - v00), r1 = v10 + ax (v11 - v10), K = r0 + ay (r1 - r0).
+ * With a map, compass_find, compass_fit and ut_run_batched use per track
+ *   window half-width  K qop_max |z_l - z_kink| + tol_win,
+ *   slope cut          K qop_max + tol_slope,
+ *   output q/p         (fitted kick coefficient) * kick_k / K,
+ * in place of the same expressions with the constant compass_params.kick_k
+ * (the chi2, x and tx do not depend on the kick's scale).  The values are
+ * copied (synchronously) to device memory owned by the context.  nx = 0
+ * removes the map.  Errors: UT_ERR_ARG for nx or ny outside [2, 256],
+ * non-positive or non-finite ranges or values; UT_ERR_CUDA if the copy
+ * fails (the previous map stays).  Launches read the map's device copy
+ * when they run: a CUDA graph captured with a map must be captured again
+ * after the map is replaced or removed (replacing frees the old copy).
+ * The serving engine's contexts have no map.
+ */
+int ut_ctx_set_kick_map(ut_ctx* ctx, int nx, int ny, float tx_max, float ty_max, const float* host_values);
+
 /* Synchronise `stream`, then report the recorded device error (0 if none):
  * *code = UT_ERR_*, *where_a = event (-1 if global), *where_b = bank or
  * track index within the event (-1 if global).  Does not clear it. */

@@ -23,7 +23,7 @@ UT_ERR_CAPACITY, UT_ERR_WIN16, UT_ERR_TIMEOUT, UT_ERR_CUDA = -5, -6, -7, -8
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPACITY",
              -6: "WIN16", -7: "TIMEOUT", -8: "CUDA"}
 
-EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_status", "ut_status_reset",
+EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
            "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate")
@@ -100,6 +100,7 @@ def lib():
             sig = {
                 "ut_ctx_create": ([P, P], I),
                 "ut_ctx_destroy": ([P], I),
+                "ut_ctx_set_kick_map": ([P, I, I, ctypes.c_float, ctypes.c_float, P], I),
                 "ut_status": ([P, P, P, P, P], I),
                 "ut_status_reset": ([P, P], I),
                 "ut_decode_workspace_size": ([I], SZ),
@@ -197,6 +198,19 @@ class Context:
 
     def reset(self, stream=None):
         _check(lib().ut_status_reset(self.handle, _stream(stream)), "ut_status_reset")
+
+    def set_kick_map(self, kick_map=None):
+        """Field look-up table of the kick (ut_ctx_set_kick_map): an object with
+        nx, ny, tx_max, ty_max and values (float32 [ny, nx]); None removes it."""
+        if kick_map is None:
+            _check(lib().ut_ctx_set_kick_map(self.handle, 0, 0, 0.0, 0.0, None), "ut_ctx_set_kick_map")
+            return
+        v = np.ascontiguousarray(kick_map.values, dtype=np.float32)
+        if v.shape != (int(kick_map.ny), int(kick_map.nx)):
+            raise ValueError("kick map values must have shape (ny, nx)")
+        _check(lib().ut_ctx_set_kick_map(self.handle, int(kick_map.nx), int(kick_map.ny),
+                                         float(kick_map.tx_max), float(kick_map.ty_max),
+                                         v.ctypes.data_as(ctypes.c_void_p)), "ut_ctx_set_kick_map")
 
     def check(self, stream=None, what="device"):
         code, a, b = self.status(stream)

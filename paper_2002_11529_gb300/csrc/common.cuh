@@ -123,6 +123,10 @@ struct ut_ctx {
     int device;
     int num_sms;
     int smem_optin;  // largest dynamic shared memory a block may opt in to
+    // kick map (ut_ctx_set_kick_map): nx = 0 when none
+    float* d_kmap;
+    int kmap_nx, kmap_ny;
+    float kmap_tx_max, kmap_ty_max, kmap_max;
 };
 
 namespace utc {

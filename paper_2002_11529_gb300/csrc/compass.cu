@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) compass_fit_kernel(const FindArgs A) {
     float qop = 0.f, chi2 = 0.f, xo = vx, txo = vtx;
     float fa, fb, fq, c2;
     if (n >= 3 && fit32(d, present, A, &ft, fa, fb, fq, c2)) {
-        qop = fq;
+        qop = A.kmap ? fq * (A.kick_k / kick_at(A, vtx, vty)) : fq;
         chi2 = c2;
         xo = vx + fa;
         txo = vtx + fb;
@@ -163,6 +163,28 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
         A.band_k2[dir] = q != 0.f ? r / q : 0.f;
     }
     A.x_cap = 0;
+    // kick map: per-track kick; hw[] bounds the search hints with the map's
+    // largest value (slightly widened)
+    A.kmap = ctx->kmap_nx ? ctx->d_kmap : nullptr;
+    A.kmap_nx = ctx->kmap_nx;
+    A.kmap_ny = ctx->kmap_ny;
+    A.kmap_tx_max = ctx->kmap_tx_max;
+    A.kmap_ty_max = ctx->kmap_ty_max;
+    A.kmap_sx = ctx->kmap_nx ? (float)(ctx->kmap_nx - 1) / (2.0f * ctx->kmap_tx_max) : 0.f;
+    A.kmap_sy = ctx->kmap_nx ? (float)(ctx->kmap_ny - 1) / (2.0f * ctx->kmap_ty_max) : 0.f;
+    A.kick_k = p->kick_k;
+    A.qop_max = p->qop_max;
+    A.tol_win = p->tol_win;
+    A.tol_slope = p->tol_slope;
+    for (int l = 0; l < 4; ++l) A.adz[l] = fabsf(g.z[l] - p->z_kink);
+    if (A.kmap) {
+        const float kmax = ctx->kmap_max * 1.0001f;
+        const float kqm = kmax * p->qop_max;
+        for (int l = 0; l < 4; ++l) {
+            const float hwm = kqm * A.adz[l] + p->tol_win;
+            A.hw[l] = hwm > A.hw[l] ? hwm : A.hw[l];
+        }
+    }
     A.split = 1;
     // fit factors per presence mask (float, operations in the fit's order)
     for (int l = 0; l < 4; ++l) {

@@ -75,7 +75,33 @@ struct FindArgs {
     float fac[16][6];
     int fac_ok[16];
     float wt[4], wf[4];
+    // Kick map (ut_ctx_set_kick_map; kmap == nullptr: the constant kick).
+    // hw[] above then holds the half-widths of the map's largest value (the
+    // bounds of the search hints), and each track gets its own.
+    const float* kmap;
+    int kmap_nx, kmap_ny;
+    float kmap_tx_max, kmap_ty_max, kmap_sx, kmap_sy;
+    float kick_k, qop_max, tol_win, tol_slope;
+    float adz[4];                // |z_l - z_kink|
 };
+
+// The kick of a track of direction (tx, ty) from the map: bilinear
+// interpolation, coordinates clamped to the grid, float operations in the
+// order of the C ABI's definition.
+__device__ __forceinline__ float kick_at(const FindArgs& A, float tx, float ty) {
+    const int nx = A.kmap_nx, ny = A.kmap_ny;
+    float fx = (tx + A.kmap_tx_max) * A.kmap_sx;
+    float fy = (ty + A.kmap_ty_max) * A.kmap_sy;
+    fx = fminf(fmaxf(fx, 0.0f), (float)(nx - 1));
+    fy = fminf(fmaxf(fy, 0.0f), (float)(ny - 1));
+    const int ix = min((int)fx, nx - 2), iy = min((int)fy, ny - 2);
+    const float ax = fx - (float)ix, ay = fy - (float)iy;
+    const float* v = A.kmap + iy * nx + ix;
+    const float v00 = __ldg(v), v01 = __ldg(v + 1), v10 = __ldg(v + nx), v11 = __ldg(v + nx + 1);
+    const float r0 = v00 + ax * (v01 - v00);
+    const float r1 = v10 + ax * (v11 - v10);
+    return r0 + ay * (r1 - r0);
+}
 
 // Track prediction in the measured coordinate of layer l:
 // u_l = x_v(z_l) - y_v(z_l) * tan(a_l) in double, split into (hi, lo).
@@ -187,6 +213,8 @@ struct GroupHead {
     int rpos[4];                 // record of the best tracklet of the warp search
     float ra, rb, rq, rc2;
     int rnh;
+    float stol;                  // kick map: the track's slope cut
+    float qscale;                // kick map: kick_k / K (q/p per fitted kick coefficient)
 };
 
 // Pairs (first anchor, second anchor) of a warp waiting for evaluation.
@@ -280,7 +308,7 @@ __device__ __forceinline__ bool eval_pair(const FindArgs& A, const View& V, int 
     const float dzab = A.z[lb] - A.z[la];
     const float dzk = A.z_kink - A.z[la];
     const float sr = (db - da) / dzab;
-    if (!(fabsf(sr) <= A.slope_tol)) return false;
+    if (!(fabsf(sr) <= (A.kmap ? V.h->stol : A.slope_tol))) return false;
     const float dk = da + sr * dzk;
     if (!(fabsf(dk) <= A.tol_kink)) return false;
     float dl[4] = {0.f, 0.f, 0.f, 0.f};
@@ -641,9 +669,15 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
         const float uh = __shfl_sync(gmask, mine.hi, l, G), ul = __shfl_sync(gmask, mine.lo, l, G);
         const int c = __shfl_sync(gmask, mine.c, l, G);
         const int s0 = max(c - n_sec / 2, 0), s1 = min(c + (n_sec - 1) / 2, S - 1);
+        // half-width: the constant kick's, or the track's kick from the map
+        float hw = A.hw[l], kqt = 0.f, kick = 0.f;
+        if (A.kmap) {
+            kick = kick_at(A, vtx, vty);
+            kqt = kick * A.qop_max;
+            hw = kqt * A.adz[l] + A.tol_win;
+        }
         int w0 = 0, w1 = 0;
         if (gl < (G >= 8 ? 8 : 4)) {
-            const float hw = A.hw[l];
             const int ra = (int)off[l * S + s0], rb = (int)off[l * S + s1 + 1];
             int a = ra, b = rb;
             if (G < 8 || gl < 4) {
@@ -668,9 +702,13 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
             head->wunion[l][1] = w1;
             head->sec0[l] = s0;
             head->cen[l] = c;
-            head->scale[l] = w1 > w0 ? (float)(w1 - w0) / (2.f * A.hw[l]) : 0.f;
+            head->scale[l] = w1 > w0 ? (float)(w1 - w0) / (2.f * hw) : 0.f;
             head->hi[l] = uh;
             head->lo[l] = ul;
+            if (A.kmap && gl == 0) {
+                head->stol = kqt + A.tol_slope;
+                head->qscale = A.kick_k / kick;
+            }
             // the slot windows of layer l in slot order c, c-1, c+1, c-2, c+2
             // (each sector's part of the union) and their combined-range starts
             int pre = 0;
@@ -1005,7 +1043,7 @@ __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* f
     }
 #pragma unroll
     for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.pos[l] >= 0 ? (int)(hb + tk.pos[l]) : -1;
-    A.qop[t] = tk.q;
+    A.qop[t] = A.kmap ? tk.q * head->qscale : tk.q;
     A.chi2[t] = tk.chi2;
     A.xo[t] = vx + tk.a;
     A.txo[t] = vtx + tk.b;

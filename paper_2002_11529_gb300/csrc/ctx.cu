@@ -1,4 +1,5 @@
 // Context: geometry copy, device status word, status read-back.
+#include <cmath>
 #include <new>
 
 #include "common.cuh"
@@ -35,9 +36,40 @@ extern "C" int ut_ctx_create(ut_ctx** out, const ut_geometry* geom) {
 
 extern "C" int ut_ctx_destroy(ut_ctx* c) {
     if (!c) return UT_ERR_ARG;
+    if (c->d_kmap) cudaFree(c->d_kmap);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
     delete c;
+    return UT_OK;
+}
+
+extern "C" int ut_ctx_set_kick_map(ut_ctx* c, int nx, int ny, float tx_max, float ty_max, const float* values) {
+    if (!c) return UT_ERR_ARG;
+    if (nx == 0) {
+        c->kmap_nx = c->kmap_ny = 0;
+        return UT_OK;
+    }
+    if (nx < 2 || nx > 256 || ny < 2 || ny > 256 || !values || !(tx_max > 0.f) || !(ty_max > 0.f) ||
+        !std::isfinite(tx_max) || !std::isfinite(ty_max))
+        return UT_ERR_ARG;
+    float vmax = 0.f;
+    for (int i = 0; i < nx * ny; ++i) {
+        if (!(values[i] > 0.f) || !std::isfinite(values[i])) return UT_ERR_ARG;
+        vmax = values[i] > vmax ? values[i] : vmax;
+    }
+    float* d = nullptr;
+    if (cudaMalloc(&d, sizeof(float) * (size_t)nx * ny) != cudaSuccess) return UT_ERR_CUDA;
+    if (cudaMemcpy(d, values, sizeof(float) * (size_t)nx * ny, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return UT_ERR_CUDA;
+    }
+    if (c->d_kmap) cudaFree(c->d_kmap);
+    c->d_kmap = d;
+    c->kmap_nx = nx;
+    c->kmap_ny = ny;
+    c->kmap_tx_max = tx_max;
+    c->kmap_ty_max = ty_max;
+    c->kmap_max = vmax;
     return UT_OK;
 }
 

@@ -27,9 +27,9 @@ def sorted_to_raw(batch) -> np.ndarray:
     return np.lexsort((batch.truth_h.astype(np.int64), bank))
 
 
-def evaluate(batch, tracks: dict) -> dict:
-    """tracks: the track slots (numpy: hit [T,4] sorted-hit indices or -1,
-    found [T]) of `batch`.  Returns counts and rates."""
+def own_track(batch, tracks: dict) -> np.ndarray:
+    """Per track slot: found, and at least 70 % of its UT hits come from the
+    particle of its own VELO track (reconstructed)."""
     T = batch.n_tracks
     hit = np.asarray(tracks["hit"])[:T]
     found = np.asarray(tracks["found"])[:T].astype(bool)
@@ -40,7 +40,16 @@ def evaluate(batch, tracks: dict) -> dict:
     owner[present] = owner_raw[perm[hit[present]]]
     nh = present.sum(axis=1)
     own = (present & (owner == np.arange(T)[:, None])).sum(axis=1)
-    correct = found & (nh > 0) & (own >= RECONSTRUCTED_FRACTION * np.maximum(nh, 1))
+    return found & (nh > 0) & (own >= RECONSTRUCTED_FRACTION * np.maximum(nh, 1))
+
+
+def evaluate(batch, tracks: dict) -> dict:
+    """tracks: the track slots (numpy: hit [T,4] sorted-hit indices or -1,
+    found [T]) of `batch`.  Returns counts and rates."""
+    T = batch.n_tracks
+    found = np.asarray(tracks["found"])[:T].astype(bool)
+    owner_raw = np.asarray(batch.truth_track, np.int64)
+    correct = own_track(batch, tracks)
     fake = found & ~correct
     # reconstructible: true hits in >= 3 layers, forward VELO track
     sig = owner_raw >= 0
