@@ -131,7 +131,7 @@ int orc_decode(const uint32_t* raw, uint64_t n_words, const uint64_t* ev_off, in
     int* ev_err_bank = (int*)calloc((size_t)E, sizeof(int));
     if (!n_bank || !ev_err || !ev_err_bank) { free(n_bank); free(ev_err); free(ev_err_bank); return ORC_ERR_ARG; }
 
-    /* Pass 1: hit counts per bank ("calculate number of hits"). */
+    /* Pass 1: hit counts per bank (the hit-counting kernel of Table I). */
 #pragma omp parallel for schedule(dynamic, 4)
     for (int e = 0; e < E; ++e) {
         /* an event must lie inside the buffer and hold its directory */
