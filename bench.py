@@ -55,7 +55,8 @@ def parse():
                     help="batched form: use --tracks-per-warp/--block instead of the autotuner's pick")
     ap.add_argument("--x-cap", type=int, default=8192)
     ap.add_argument("--tracks-per-warp", type=int, default=8)
-    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--block", type=int, default=None,
+                    help="threads per block (default: 800 at 8 tracks per warp, else 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the uneven-workload form comparison, serving and alignment measurements")
@@ -263,7 +264,8 @@ def time_forms_on_uneven_workload(g, params, flush, steps=5):
         return statistics.median(ms)
 
     ms_b = timed(runner.replay)
-    ms_p = timed(lambda: pipe.run_plain(stream, cfg.tracks_per_warp, 256))
+    blk_p = 800 if cfg.tracks_per_warp == 8 else 256   # compass_find's best block at that width
+    ms_p = timed(lambda: pipe.run_plain(stream, cfg.tracks_per_warp, blk_p))
     ctx.check(stream, "uneven workload")
     E = batch.n_events
     out = {"workload": f"{E} events, hits/event lognormal (median 3000, sigma 0.6, 500-15000), "
@@ -271,7 +273,8 @@ def time_forms_on_uneven_workload(g, params, flush, steps=5):
            "batched_form": {"ms": round(ms_b, 4), "events_per_s": E / ms_b * 1e3,
                             "launch": {"tracks_per_warp": cfg.tracks_per_warp, "block": cfg.block,
                                        "graph": True, "kernels_per_step": 1}},
-           "plain_form": {"ms": round(ms_p, 4), "events_per_s": E / ms_p * 1e3, "kernels_per_step": 4},
+           "plain_form": {"ms": round(ms_p, 4), "events_per_s": E / ms_p * 1e3, "kernels_per_step": 4,
+                          "compass_find_block": blk_p},
            "batched_over_plain": ms_p / ms_b}
     ctx.close()
     return out
@@ -369,7 +372,8 @@ def physics_sweep(g, batch, params, reps=5):
     """The paper's trade-off table on the synthetic workload: for
     n_sectors in {1, 3, 5} and n_candidates in {1, 2, 4, 8, 16}, the track
     finding efficiency and fake rate on generator truth, and the events/s
-    of the sorted decode + compass_find (8 tracks per warp, L2 flushed)."""
+    of the sorted decode + compass_find (8 tracks per warp, 800 threads, L2
+    flushed)."""
     import numpy as np
     import torch
     from paper_2002_11529_gb300 import physics
@@ -387,7 +391,7 @@ def physics_sweep(g, batch, params, reps=5):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, True, pipe.workspace)
-                g.compass_find(ctx, pipe.hits_a, pipe.velo, E, p, pipe.tracks, tracks_per_warp=8)
+                g.compass_find(ctx, pipe.hits_a, pipe.velo, E, p, pipe.tracks, tracks_per_warp=8, block=800)
                 e1.record()
                 e1.synchronize()
                 if r:
@@ -548,7 +552,8 @@ def main():
     pipe = g.Pipeline(ctx, batch, params)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-    tpw, blk = args.tracks_per_warp, args.block
+    tpw = args.tracks_per_warp
+    blk = args.block if args.block is not None else (800 if tpw == 8 else 256)
     E = batch.n_events
 
     kern = {"plain": ["ut_decode", "ut_sort_hits", "compass_find", "compass_fit"],

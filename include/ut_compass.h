@@ -238,7 +238,10 @@ int ut_sort_hits(ut_ctx* ctx, const ut_hits* in, ut_hits* out, uint32_t* d_perm,
  * relative to the event's layer start, size), (-1, -1) when empty;
  * UT_ERR_WIN16 is recorded if a value does not fit.
  * Launch shape: `tracks_per_warp` in {1, 2, 4, 8} (0 = default 1) and
- * `block` threads in {64..1024, multiple of 32} (0 = default 256).
+ * `block` threads, a multiple of 32 from 64 to 256 (0 = default 256), or,
+ * with tracks_per_warp 8, up to 800 (one block per SM: 25 warps cover an
+ * event of 200 tracks in one round of warp calls).  Other shapes return
+ * UT_ERR_ARG before any launch.
  */
 int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int n_events,
                  uint32_t n_tracks, const compass_params* p, compass_tracks* out,

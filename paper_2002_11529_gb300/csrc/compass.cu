@@ -15,7 +15,7 @@
 namespace utc {
 
 template <int G>
-__global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A) {
+__device__ __forceinline__ void compass_event_body(const FindArgs& A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int S = A.S, B = 4 * S;
     const int nt = blockDim.x;
@@ -54,6 +54,20 @@ __global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A)
         const uint32_t k = tw + (uint32_t)(g - gw);
         compass_warp<G>(A, heads + gw, ft, Q, X, soff, hb, e, t0 + k, k < wb, search, gl, gmask);
     }
+}
+
+// Blocks of 64-256 threads, two per SM (128 registers a thread).
+template <int G>
+__global__ void __launch_bounds__(256, 2) compass_event_kernel(const FindArgs A) {
+    compass_event_body<G>(A);
+}
+
+// Large blocks (8 tracks per warp): 288-800 threads, one per SM, so that the
+// warps of one block cover an event's tracks in fewer rounds of warp calls
+// (800 threads: 25 warps x 8 = 200 tracks in one round).
+constexpr int kFindLargeMax = 800;
+__global__ void __launch_bounds__(kFindLargeMax, 1) compass_event_large_kernel(const FindArgs A) {
+    compass_event_body<4>(A);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,8 +253,11 @@ static int launch_find(FindArgs A, int block, int num_sms, cudaStream_t st) {
     const size_t off_bytes = ((size_t)(B + 1) * 4 + 15) & ~(size_t)15;
     const size_t smem = off_bytes + (size_t)gpb * sizeof(GroupHead) + (size_t)(block / 32) * sizeof(PairQueue) +
                         sizeof(FitTable) + (size_t)A.x_cap * sizeof(float);
-    if (cudaFuncSetAttribute(compass_event_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    void (*kern)(const FindArgs) = compass_event_kernel<G>;
+    if constexpr (G == 4) {
+        if (block > 256) kern = compass_event_large_kernel;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
     // One block per part of an event: an event's tracks are split so that
     // about two warp calls of tracks remain per warp (tracks of one warp call
@@ -251,7 +268,7 @@ static int launch_find(FindArgs A, int block, int num_sms, cudaStream_t st) {
     const long long units = (long long)A.n_events * A.split;
     if (units > 0x7fffffffll) return UT_ERR_ARG;
     const int grid = (int)units;
-    compass_event_kernel<G><<<grid, block, smem, st>>>(A);
+    kern<<<grid, block, smem, st>>>(A);
     return check_cuda(cudaGetLastError());
 }
 
@@ -269,7 +286,8 @@ extern "C" int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
     if (n_tracks == 0 || n_events == 0) return UT_OK;
     if (tracks_per_warp == 0) tracks_per_warp = 1;
     if (block == 0) block = 256;
-    if (block < 64 || block > 256 || block % 32 != 0) return UT_ERR_ARG;
+    if (block < 64 || block % 32 != 0) return UT_ERR_ARG;
+    if (block > 256 && (tracks_per_warp != 8 || block > kFindLargeMax)) return UT_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (tracks_per_warp) {
         case 1: return launch_find<32>(A, block, ctx->num_sms, st);

@@ -242,12 +242,39 @@ def test_compass_find_matches_oracle(g, name):
     assert_tracks_equal(gpu, orc, b)
 
 
-@pytest.mark.parametrize("tpw,block", [(1, 128), (2, 256), (4, 256), (4, 64), (8, 256), (8, 128)])
+@pytest.mark.parametrize("tpw,block", [(1, 128), (2, 256), (4, 256), (4, 64), (8, 256), (8, 128),
+                                       (8, 288), (8, 544), (8, 800)])
 def test_compass_launch_shapes(g, tpw, block):
     b = BATCHES["plain64"]()
     gpu = run_compass(g, b, P, tracks_per_warp=tpw, block=block)
     _, orc = oracle.run_batch(b, P)
     assert_tracks_equal(gpu, orc, b, report=False)
+
+
+@pytest.mark.parametrize("name", ["lognormal200", "dense"])
+def test_compass_large_block_on_uneven_events(g, name):
+    """800-thread blocks on events of very different track counts (several
+    rounds of warp calls, or warps without tracks)."""
+    b = BATCHES[name]()
+    gpu = run_compass(g, b, P, tracks_per_warp=8, block=800, want_windows=True)
+    _, orc = oracle.run_batch(b, P, want_windows=True)
+    assert_tracks_equal(gpu, orc, b, report=False)
+    assert np.array_equal(gpu["win"], orc.win)
+
+
+@pytest.mark.parametrize("tpw,block", [(4, 512), (1, 288), (8, 832), (8, 300), (8, 32)])
+def test_compass_rejects_unsupported_shapes(g, tpw, block):
+    """Blocks above 256 threads exist for 8 tracks per warp only, up to 800
+    threads, multiples of 32: other shapes return UT_ERR_ARG before any
+    launch."""
+    b = BATCHES["tiny"]()
+    ctx = ctx_for(g, b.geom)
+    pipe = g.Pipeline(ctx, b, P)
+    g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, b.n_events, pipe.hits_a, True, pipe.workspace)
+    with pytest.raises(g.UtError) as err:
+        g.compass_find(ctx, pipe.hits_a, pipe.velo, b.n_events, P, pipe.tracks, tracks_per_warp=tpw, block=block)
+    assert err.value.code == g.UT_ERR_ARG
+    assert ctx.status()[0] == 0
 
 
 @pytest.mark.parametrize("n_sec,n_cand", [(1, 1), (3, 2), (3, 16), (5, 1), (5, 16)])
