@@ -360,3 +360,66 @@ def align_refit(hits, track_hits, geom, velo, params, align):
                           *(_p(v) for v in vel), ctypes.byref(pp), _p(np.ascontiguousarray(align, np.float64)),
                           _p(out))
     return out[:T]
+
+
+@dataclasses.dataclass
+class GroupHits:
+    """Hits of the sector-group decoding, in output order (event, layer,
+    group, then yBegin, then raw order)."""
+    x: np.ndarray         # f32, x at y = 0
+    z: np.ndarray         # f32, z of the plane
+    y_begin: np.ndarray   # f32
+    y_end: np.ndarray     # f32
+    weight: np.ndarray    # f32, 1 / sigma^2 of the position
+    id: np.ndarray        # u32, (layer << 24) | (sensor << 16) | word
+    group_off: np.ndarray  # u32[E * 4 * n_groups + 1]
+    src: np.ndarray       # i64, index of each output hit in the bank-order decode
+
+
+def decode_groups(raw, ev_off, n_events, gg, n_threads=0):
+    """Sector-group decoding (Sec. IV; Table I's pre-decode, find permutation
+    and decode-in-order kernels): every hit's x at y = 0 and z, its strip's
+    y range [yBegin, yEnd] (its sensor's rows), its weight, and its sector
+    group (the x region holding x); hits stored by (event, layer, group)
+    with offsets, sorted by yBegin inside a group (stable: ties keep the raw
+    order).  `gg`: synth.grouped.GroupGeometry.  The raw banks are checked
+    and read by the bank-order decode (one sector per sensor); the rest is
+    written out here in float32, each operation as stated."""
+    rg = gg.raw_geometry()
+    code, h, where = decode(raw, ev_off, n_events, rg, sorted_=False, n_threads=n_threads)
+    if code != 0:
+        raise OracleError(code, where)
+    n = int(h.n)
+    ids = h.id[:n].astype(np.int64)
+    R = int(gg.rows)
+    S2 = int(gg.n_columns) * R
+    NG = int(gg.n_groups)
+    layer = ids >> 24
+    sensor = (ids >> 16) & 0xFF
+    word = ids & 0xFFFF
+    col = sensor // R
+    row = sensor % R
+    half = 2 * (word & 0x3FF) + ((word >> 10) & 1)
+    f32 = np.float32
+    # x at y = 0 (as the base decode, per column): x0 = c * pitch + x_min; x = x0 + (h + 1/2) * (pitch/2)
+    x0 = col.astype(f32) * f32(gg.base.sector_pitch) + f32(gg.x_min)
+    hp = f32(gg.base.strip_pitch) * f32(0.5)
+    x = x0 + (half.astype(f32) + f32(0.5)) * hp
+    z = np.asarray(gg.base.z, f32)[layer]
+    H = f32(gg.sensor_height)
+    yb = f32(gg.y_min) + row.astype(f32) * H
+    ye = yb + H
+    sig = f32(np.float64(f32(gg.base.strip_pitch)) / np.sqrt(12.0))   # the float pitch, / sqrt(12) in double
+    w = np.full(n, f32(1.0) / (sig * sig), f32)
+    edges = gg.group_edges()
+    grp = np.searchsorted(edges[1:-1], x, side="right").astype(np.int64)   # interior edges <= x
+    B = 4 * S2
+    bank_first = h.hit_off[: n_events * B : B].astype(np.int64)           # first hit of each event
+    event = np.searchsorted(bank_first, np.arange(n), side="right") - 1 if n else np.zeros(0, np.int64)
+    order = np.lexsort((np.arange(n), yb, grp, layer, event))
+    cell = (event * 4 + layer) * NG + grp
+    counts = np.bincount(cell, minlength=n_events * 4 * NG)
+    goff = np.zeros(n_events * 4 * NG + 1, np.int64)
+    goff[1:] = np.cumsum(counts)
+    return GroupHits(x[order], z[order], yb[order], ye[order], w[order], h.id[:n][order],
+                     goff.astype(np.uint32), order.astype(np.int64))

@@ -1,0 +1,79 @@
+"""Pins of the oracle's sector-group decoding (Sec. IV, Table I): hits
+against the generator's truth, the group and row geometry, the order inside
+a group, the offsets."""
+import numpy as np
+
+import oracle
+from synth.grouped import generate_grouped
+
+
+def _batch(**kw):
+    return generate_grouped(6, seed=5, **kw)
+
+
+def test_every_generated_hit_once_with_its_sensor_and_strip():
+    b = _batch()
+    gh = oracle.decode_groups(b.raw, b.ev_off, b.n_events, b.geom)
+    n = int(b.bank_n.sum())
+    assert gh.x.size == n and gh.group_off[-1] == n
+    assert np.array_equal(np.sort(gh.src), np.arange(n))
+    ids = gh.id.astype(np.int64)
+    R = b.geom.rows
+    assert np.array_equal(ids >> 24, b.truth_layer[gh.src])
+    assert np.array_equal((ids >> 16) & 0xFF, b.truth_column[gh.src].astype(np.int64) * R + b.truth_row[gh.src])
+    half = 2 * (ids & 0x3FF) + ((ids >> 10) & 1)
+    assert np.array_equal(half, b.truth_h[gh.src])
+
+
+def test_positions_rows_and_weights():
+    b = _batch()
+    g = b.geom
+    gh = oracle.decode_groups(b.raw, b.ev_off, b.n_events, g)
+    col = b.truth_column[gh.src].astype(np.float64)
+    lo = g.x_min + col * 96.0
+    assert np.all(gh.x >= lo) and np.all(gh.x < lo + 512 * 0.187 + 1e-3)
+    assert np.array_equal(gh.z, np.asarray(g.base.z, np.float32)[b.truth_layer[gh.src]])
+    r = b.truth_row[gh.src].astype(np.float64)
+    assert np.array_equal(gh.y_begin.astype(np.float64), g.y_min + r * g.sensor_height)
+    assert np.array_equal(gh.y_end - gh.y_begin, np.full(gh.x.size, np.float32(g.sensor_height)))
+    # the track's true y at the plane lies in its hit's strip range
+    y = b.truth_y[gh.src]
+    sig = ~np.isnan(y)
+    assert sig.sum() > 100
+    assert np.all((y[sig] >= gh.y_begin[sig]) & (y[sig] < gh.y_end[sig]))
+    # weight = 1 / sigma^2 with sigma = pitch / sqrt(12)
+    np.testing.assert_allclose(gh.weight, 12.0 / 0.187 ** 2, rtol=1e-6)
+
+
+def test_groups_hold_their_x_region_and_are_narrow_in_the_centre():
+    b = _batch()
+    g = b.geom
+    e = g.group_edges().astype(np.float64)
+    w = np.diff(e)
+    half = g.n_groups // 2
+    assert np.all(np.diff(w[half:]) > 0) and np.all(np.diff(w[:half]) < 0)   # widening outwards
+    assert e[0] == g.x_min and np.isclose(e[-1], -g.x_min)
+    gh = oracle.decode_groups(b.raw, b.ev_off, b.n_events, g)
+    NG = g.n_groups
+    for cell in range(b.n_events * 4 * NG):
+        a, z = int(gh.group_off[cell]), int(gh.group_off[cell + 1])
+        if a == z:
+            continue
+        k = cell % NG
+        l = (cell // NG) % 4
+        x = gh.x[a:z].astype(np.float64)
+        assert np.all((x >= e[k]) & (x < e[k + 1]) | ((k == NG - 1) & (x >= e[k])))
+        assert np.all((gh.id[a:z].astype(np.int64) >> 24) == l)
+        yb = gh.y_begin[a:z]
+        assert np.all(np.diff(yb) >= 0)
+        ties = np.diff(yb) == 0
+        assert np.all(np.diff(gh.src[a:z])[ties] > 0)   # stable: raw order among equal yBegin
+
+
+def test_event_offsets_match_the_banks():
+    b = _batch(rows=3, n_groups=10)
+    g = b.geom
+    gh = oracle.decode_groups(b.raw, b.ev_off, b.n_events, g)
+    per_event = b.bank_n.reshape(b.n_events, g.n_banks).sum(axis=1)
+    assert np.array_equal(np.diff(gh.group_off[np.arange(0, b.n_events * 4 * g.n_groups + 1, 4 * g.n_groups)]),
+                          per_event)
