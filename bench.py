@@ -158,13 +158,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def source_digest():
-    """sha256 over the CUDA sources and the ABI header (sorted by name)."""
+# The sources each measured kernel is built and launched from: its .cu
+# file, the device headers it includes, the ABI header, and the host code
+# that fills its arguments (make_find_args in compass.cu) or sizes its grid
+# (the context in ctx.cu).
+KERNEL_SOURCES = {
+    "ut_run_batched": ("batched.cu", "compass.cu", "compass_track.cuh", "decode_event.cuh", "common.cuh",
+                       "ctx.cu", "../../include/ut_compass.h"),
+    "compass_find": ("compass.cu", "compass_track.cuh", "common.cuh", "ctx.cu", "../../include/ut_compass.h"),
+    "ut_decode": ("decode.cu", "decode_event.cuh", "common.cuh", "ctx.cu", "../../include/ut_compass.h"),
+}
+
+
+def source_digest(kernel):
+    """sha256 over the sources of one measured kernel (KERNEL_SOURCES)."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2002_11529_gb300", "csrc", "*.cu*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
-    for path in files:
+    csrc = os.path.join(ROOT, "paper_2002_11529_gb300", "csrc")
+    for rel in sorted(KERNEL_SOURCES[kernel]):
+        path = os.path.normpath(os.path.join(csrc, rel))
         h.update(os.path.basename(path).encode())
         with open(path, "rb") as f:
             h.update(f.read())
@@ -180,7 +192,7 @@ def measured_traffic(kernel, workload):
             rec = json.load(f).get(f"{kernel}|{workload}")
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_sha256") != source_digest():
+    if not rec or kernel not in KERNEL_SOURCES or rec.get("source_sha256") != source_digest(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 

@@ -26,7 +26,8 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPA
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
-           "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate")
+           "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate",
+           "ut_sector_groups")
 
 
 class UtGeometry(ctypes.Structure):
@@ -40,6 +41,18 @@ class UtHits(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("z", ctypes.c_void_p), ("sector", ctypes.c_void_p),
                 ("layer", ctypes.c_void_p), ("id", ctypes.c_void_p), ("hit_off", ctypes.c_void_p),
                 ("capacity", ctypes.c_uint32)]
+
+
+class UtGroupGeometry(ctypes.Structure):
+    _fields_ = [("n_columns", ctypes.c_int), ("rows", ctypes.c_int), ("n_groups", ctypes.c_int),
+                ("sector_pitch", ctypes.c_float), ("strip_pitch", ctypes.c_float), ("x_min", ctypes.c_float),
+                ("y_min", ctypes.c_float), ("sensor_height", ctypes.c_float), ("z", ctypes.c_float * 4),
+                ("edges", ctypes.c_float * 129)]
+
+
+class UtGroupHits(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("x", "z", "y_begin", "y_end", "weight", "id", "group_off")] + [
+        ("capacity", ctypes.c_uint32)]
 
 
 class VeloTracks(ctypes.Structure):
@@ -113,6 +126,7 @@ def lib():
                 "ut_align_workspace_size": ([I], SZ),
                 "ut_consolidate_workspace_size": ([I], SZ),
                 "ut_consolidate": ([P, P, I, P, P, P, P, SZ, P], I),
+                "ut_sector_groups": ([P, P, I, P, P, P], I),
                 "ut_align_chi2": ([P, P, P, P, U32, P, P, P, P, P, P, P, P, SZ, P], I),
                 "ut_align_refit": ([P, P, P, P, U32, P, P, P, P], I),
                 "ut_align_hvp": ([P, P, P, P, U32, P, P, P, P, P, P], I),
@@ -529,3 +543,76 @@ class GraphRunner:
 
     def replay(self):
         self.graph.replay()
+
+
+def group_geometry_struct(gg) -> UtGroupGeometry:
+    """ut_group_geometry of a synth.grouped.GroupGeometry."""
+    s = UtGroupGeometry()
+    s.n_columns, s.rows, s.n_groups = int(gg.n_columns), int(gg.rows), int(gg.n_groups)
+    s.sector_pitch = float(gg.base.sector_pitch)
+    s.strip_pitch = float(gg.base.strip_pitch)
+    s.x_min, s.y_min, s.sensor_height = float(gg.x_min), float(gg.y_min), float(gg.sensor_height)
+    for l in range(4):
+        s.z[l] = float(gg.base.z[l])
+    e = np.asarray(gg.group_edges(), np.float32)
+    for k, v in enumerate(e):
+        s.edges[k] = float(v)
+    return s
+
+
+@dataclasses.dataclass
+class GroupHitBuffers:
+    """Device SoA of the sector-group layout (ut_group_hits)."""
+    x: torch.Tensor
+    z: torch.Tensor
+    y_begin: torch.Tensor
+    y_end: torch.Tensor
+    weight: torch.Tensor
+    id: torch.Tensor
+    group_off: torch.Tensor
+    capacity: int
+
+    @staticmethod
+    def allocate(capacity, n_events, n_groups, device="cuda"):
+        cap = max(int(capacity), 1)
+        f = lambda: torch.empty(cap, dtype=torch.float32, device=device)
+        return GroupHitBuffers(f(), f(), f(), f(), f(), torch.empty(cap, dtype=torch.int32, device=device),
+                               torch.empty(n_events * 4 * n_groups + 1, dtype=torch.int32, device=device),
+                               int(capacity))
+
+    def struct(self) -> UtGroupHits:
+        h = UtGroupHits()
+        for n in ("x", "z", "y_begin", "y_end", "weight", "id", "group_off"):
+            setattr(h, n, getattr(self, n).data_ptr())
+        h.capacity = min(int(self.capacity), 0xFFFFFFFF)
+        return h
+
+
+def ut_sector_groups(ctx, bank_order: HitBuffers, n_events, gg, out: GroupHitBuffers, stream=None):
+    """The sector-group layout from a bank-order decode (ut_sector_groups)."""
+    h, g, o = bank_order.struct(), group_geometry_struct(gg), out.struct()
+    _check(lib().ut_sector_groups(ctx.handle, ctypes.byref(h), int(n_events), ctypes.byref(g), ctypes.byref(o),
+                                  _stream(stream)), "ut_sector_groups")
+
+
+def decode_groups(raw, ev_off, n_events, gg, stream=None):
+    """Raw banks of a grouped detector -> (Context, GroupHitBuffers): the
+    bank-order decode on a context with one sector per sensor, then
+    ut_sector_groups.  The context's status is checked."""
+    ctx = Context(gg.raw_geometry())
+    raw_d, ev_d = upload_raw(raw, ev_off)
+    nw = int(ev_off[n_events]) if n_events else 0
+    hits = HitBuffers.allocate(2 * nw + 8, n_events, gg.n_columns * gg.rows)
+    ut_decode(ctx, raw_d, nw, ev_d, n_events, hits, False, stream=stream)
+    out = GroupHitBuffers.allocate(2 * nw + 8, n_events, gg.n_groups)
+    ut_sector_groups(ctx, hits, n_events, gg, out, stream)
+    ctx.check(stream, "decode_groups")
+    return ctx, out
+
+
+def group_hits_to_numpy(gh: GroupHitBuffers):
+    off = gh.group_off.cpu().numpy().view(np.uint32)
+    n = int(off[-1])
+    return dict(x=gh.x[:n].cpu().numpy(), z=gh.z[:n].cpu().numpy(), y_begin=gh.y_begin[:n].cpu().numpy(),
+                y_end=gh.y_end[:n].cpu().numpy(), weight=gh.weight[:n].cpu().numpy(),
+                id=gh.id[:n].cpu().numpy().view(np.uint32), group_off=off)
