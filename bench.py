@@ -461,6 +461,52 @@ def measure_kick_map(g, params, cfg, reps=10):
     return res
 
 
+def measure_sector_groups(g, reps=10):
+    """ut_sector_groups (row f2, the sector-group hit layout) on 1000 events
+    of a detector with 48 columns x 4 rows of sensors per plane and 84
+    groups (200 tracks, 4000 hits per event): device time of the bank-order
+    decode and of the group pass (CUDA events, L2 flushed), and the group
+    pass's algorithmic bytes (id read, six 4-byte fields written per hit,
+    group offsets written) against the measured HBM bandwidth."""
+    import numpy as np
+    import torch
+    from synth.grouped import generate_grouped
+    b = generate_grouped(1000, n_columns=48, rows=4, n_groups=84, tracks=200, hits=4000, seed=21)
+    gg = b.geom
+    ctx = g.Context(gg.raw_geometry())
+    raw_d, ev_d = g.upload_raw(b.raw, b.ev_off)
+    nw = int(b.ev_off[-1])
+    E = b.n_events
+    hits = g.HitBuffers.allocate(2 * nw + 8, E, gg.n_columns * gg.rows)
+    out = g.GroupHitBuffers.allocate(2 * nw + 8, E, gg.n_groups)
+    ws = torch.empty((g.decode_workspace_size(E) + 15) // 16 * 4, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    t_dec, t_grp = [], []
+    for r in range(reps + 1):
+        flush.add_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        g.ut_decode(ctx, raw_d, nw, ev_d, E, hits, False, ws)
+        ev[1].record()
+        g.ut_sector_groups(ctx, hits, E, gg, out)
+        ev[2].record()
+        ev[2].synchronize()
+        if r:
+            t_dec.append(ev[0].elapsed_time(ev[1]))
+            t_grp.append(ev[1].elapsed_time(ev[2]))
+    ctx.check(what="sector groups")
+    n = int(b.bank_n.sum())
+    alg = n * (4 + 24) + (E * 4 * gg.n_groups + 1) * 4 + 2 * E * 4
+    ms = float(np.median(t_grp))
+    peak, _ = peaks()
+    ctx.close()
+    return {"workload": "1000 events, 4 planes x 48 columns x 4 rows of sensors, 84 groups, hits/event 4000, "
+                        "tracks/event 200",
+            "hits": n, "decode_bank_order_ms": float(np.median(t_dec)), "sector_groups_ms": ms,
+            "events_per_s": E / (float(np.median(t_dec)) + ms) * 1e3,
+            "algorithmic_bytes": alg, "achieved_gbs": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak}
+
+
 def measure_consolidation(g, ctx, pipe, batch, flush, reps=10):
     """ut_consolidate on the tracks of the last step: device time and the
     fraction of the measured HBM bandwidth of its algorithmic bytes (found
@@ -739,6 +785,7 @@ def main():
         line["physics_sweep"] = physics_sweep(g, batch, params)
         line["kick_map"] = measure_kick_map(g, params, cfg if args.form == "batched" else g.LaunchConfig(8, 512))
         line["consolidation"] = measure_consolidation(g, ctx, pipe, batch, flush)
+        line["sector_groups"] = measure_sector_groups(g)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
     print(json.dumps(line), flush=True)
