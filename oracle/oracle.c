@@ -462,6 +462,102 @@ static void range_push(range_t* r, uint32_t v) {
 }
 
 /*
+ * Tracklet search and selection (Sec. V-B) of one track over its candidate
+ * hits: R[l] (hit indices, in the combined order of the windows) and dv[l]
+ * (their residuals to the prediction).  Forward anchors (0,2) collecting
+ * (1,3); backward anchors (3,1) collecting (2,0) only when the forward pass
+ * found no valid tracklet.  *mm: the smallest decision margin, updated.
+ */
+static void search_tracklets(const orc_geom* g, const orc_params* p, const range_t* R, float* const* dv,
+                             const float* t, const float* f, float w, float px, float ptx, float stol,
+                             double* mm_io, int* best_n_o, float* best_chi2_o, float* best_q_o, float* best_a_o,
+                             float* best_b_o, int32_t* best_hit_o) {
+    double mm = *mm_io;
+    /* Tracklet search (Sec. V-B): forward anchors (0,2) collecting
+     * (1,3); backward anchors (3,1) collecting (2,0) only when the
+     * forward pass found no valid tracklet. */
+    static const int dirs[2][4] = {{0, 2, 1, 3}, {3, 1, 2, 0}};
+    int best_n = 0;
+    float best_chi2 = 0.f, best_q = 0.f, best_a = 0.f, best_b = 0.f;
+    int32_t best_hit[4] = {-1, -1, -1, -1};
+    for (int dir = 0; dir < 2; ++dir) {
+        const int la = dirs[dir][0], lb = dirs[dir][1];
+        const int lc[2] = {dirs[dir][2], dirs[dir][3]};
+        const float dzab = g->z[lb] - g->z[la];
+        const float dzk = p->z_kink - g->z[la];
+        const float dzc[2] = {g->z[lc[0]] - g->z[la], g->z[lc[1]] - g->z[la]};
+        int count = 0;
+        for (int ia = 0; ia < R[la].n && count < p->n_candidates; ++ia) {
+            const float da = dv[la][ia];
+            for (int ib = 0; ib < R[lb].n && count < p->n_candidates; ++ib) {
+                const float db = dv[lb][ib];
+                const float sr = (db - da) / dzab;
+                double m;
+                m = margin(fabsf(sr), stol);
+                if (m < mm) mm = m;
+                if (!(fabsf(sr) <= stol)) continue;
+                const float dk = da + sr * dzk;
+                m = margin(fabsf(dk), p->tol_kink);
+                if (m < mm) mm = m;
+                if (!(fabsf(dk) <= p->tol_kink)) continue;
+                float dl[4];
+                int present[4] = {0, 0, 0, 0};
+                int32_t hsel[4] = {-1, -1, -1, -1};
+                dl[la] = da; present[la] = 1; hsel[la] = (int32_t)R[la].idx[ia];
+                dl[lb] = db; present[lb] = 1; hsel[lb] = (int32_t)R[lb].idx[ib];
+                int nh = 2;
+                for (int ci = 0; ci < 2; ++ci) {
+                    const int l = lc[ci];
+                    const float pred = da + sr * dzc[ci];
+                    int bi = -1;
+                    float bd = 0.f;
+                    for (int j = 0; j < R[l].n; ++j) {
+                        const float dist = fabsf(dv[l][j] - pred);
+                        m = margin(dist, p->tol_col);
+                        if (m < mm) mm = m;
+                        if (!(dist <= p->tol_col)) continue;
+                        if (bi >= 0) {
+                            m = margin(dist, bd);
+                            if (m < mm) mm = m;
+                        }
+                        if (bi < 0 || dist < bd) { bi = j; bd = dist; }
+                    }
+                    if (bi >= 0) {
+                        dl[l] = dv[l][bi]; present[l] = 1; hsel[l] = (int32_t)R[l].idx[bi];
+                        ++nh;
+                    }
+                }
+                if (nh < 3) continue;
+                for (int l = 0; l < 4; ++l) if (!present[l]) dl[l] = 0.f;
+                float a, b, q, c2;
+                if (!fit32(dl, present, t, f, w, px, ptx, &a, &b, &q, &c2)) continue;
+                const float c2n = c2 / (float)(nh - 1);
+                m = margin(c2n, p->chi2ndof_max);
+                if (m < mm) mm = m;
+                if (!(c2n <= p->chi2ndof_max)) continue;
+                ++count;
+                if (best_n > 0 && nh == best_n) {
+                    m = margin(c2, best_chi2);
+                    if (m < mm) mm = m;
+                }
+                if (nh > best_n || (nh == best_n && c2 < best_chi2)) {
+                    best_n = nh; best_chi2 = c2; best_q = q; best_a = a; best_b = b;
+                    for (int l = 0; l < 4; ++l) best_hit[l] = hsel[l];
+                }
+            }
+        }
+        if (count > 0) break;
+    }
+    *mm_io = mm;
+    *best_n_o = best_n;
+    *best_chi2_o = best_chi2;
+    *best_q_o = best_q;
+    *best_a_o = best_a;
+    *best_b_o = best_b;
+    for (int l = 0; l < 4; ++l) best_hit_o[l] = best_hit[l];
+}
+
+/*
  * compass: windows + tracklet search + selection for every VELO track.
  *
  * hx: sorted hit x (per bank ascending), hit_off[E*B+1].
@@ -589,81 +685,11 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
             }
             if (!any) { near_m[tr] = mm; continue; }
 
-            /* Tracklet search (Sec. V-B): forward anchors (0,2) collecting
-             * (1,3); backward anchors (3,1) collecting (2,0) only when the
-             * forward pass found no valid tracklet. */
-            static const int dirs[2][4] = {{0, 2, 1, 3}, {3, 1, 2, 0}};
             int best_n = 0;
             float best_chi2 = 0.f, best_q = 0.f, best_a = 0.f, best_b = 0.f;
             int32_t best_hit[4] = {-1, -1, -1, -1};
-            for (int dir = 0; dir < 2; ++dir) {
-                const int la = dirs[dir][0], lb = dirs[dir][1];
-                const int lc[2] = {dirs[dir][2], dirs[dir][3]};
-                const float dzab = g->z[lb] - g->z[la];
-                const float dzk = p->z_kink - g->z[la];
-                const float dzc[2] = {g->z[lc[0]] - g->z[la], g->z[lc[1]] - g->z[la]};
-                int count = 0;
-                for (int ia = 0; ia < R[la].n && count < p->n_candidates; ++ia) {
-                    const float da = dv[la][ia];
-                    for (int ib = 0; ib < R[lb].n && count < p->n_candidates; ++ib) {
-                        const float db = dv[lb][ib];
-                        const float sr = (db - da) / dzab;
-                        double m;
-                        m = margin(fabsf(sr), stol);
-                        if (m < mm) mm = m;
-                        if (!(fabsf(sr) <= stol)) continue;
-                        const float dk = da + sr * dzk;
-                        m = margin(fabsf(dk), p->tol_kink);
-                        if (m < mm) mm = m;
-                        if (!(fabsf(dk) <= p->tol_kink)) continue;
-                        float dl[4];
-                        int present[4] = {0, 0, 0, 0};
-                        int32_t hsel[4] = {-1, -1, -1, -1};
-                        dl[la] = da; present[la] = 1; hsel[la] = (int32_t)R[la].idx[ia];
-                        dl[lb] = db; present[lb] = 1; hsel[lb] = (int32_t)R[lb].idx[ib];
-                        int nh = 2;
-                        for (int ci = 0; ci < 2; ++ci) {
-                            const int l = lc[ci];
-                            const float pred = da + sr * dzc[ci];
-                            int bi = -1;
-                            float bd = 0.f;
-                            for (int j = 0; j < R[l].n; ++j) {
-                                const float dist = fabsf(dv[l][j] - pred);
-                                m = margin(dist, p->tol_col);
-                                if (m < mm) mm = m;
-                                if (!(dist <= p->tol_col)) continue;
-                                if (bi >= 0) {
-                                    m = margin(dist, bd);
-                                    if (m < mm) mm = m;
-                                }
-                                if (bi < 0 || dist < bd) { bi = j; bd = dist; }
-                            }
-                            if (bi >= 0) {
-                                dl[l] = dv[l][bi]; present[l] = 1; hsel[l] = (int32_t)R[l].idx[bi];
-                                ++nh;
-                            }
-                        }
-                        if (nh < 3) continue;
-                        for (int l = 0; l < 4; ++l) if (!present[l]) dl[l] = 0.f;
-                        float a, b, q, c2;
-                        if (!fit32(dl, present, t, f, w, px, ptx, &a, &b, &q, &c2)) continue;
-                        const float c2n = c2 / (float)(nh - 1);
-                        m = margin(c2n, p->chi2ndof_max);
-                        if (m < mm) mm = m;
-                        if (!(c2n <= p->chi2ndof_max)) continue;
-                        ++count;
-                        if (best_n > 0 && nh == best_n) {
-                            m = margin(c2, best_chi2);
-                            if (m < mm) mm = m;
-                        }
-                        if (nh > best_n || (nh == best_n && c2 < best_chi2)) {
-                            best_n = nh; best_chi2 = c2; best_q = q; best_a = a; best_b = b;
-                            for (int l = 0; l < 4; ++l) best_hit[l] = hsel[l];
-                        }
-                    }
-                }
-                if (count > 0) break;
-            }
+            search_tracklets(g, p, R, dv, t, f, w, px, ptx, stol, &mm, &best_n, &best_chi2, &best_q, &best_a,
+                             &best_b, best_hit);
             near_m[tr] = mm;
             if (best_n == 0) continue;
             for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = best_hit[l];
