@@ -77,6 +77,9 @@ def lib():
             _lib.orc_fit32_d.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, P]
             _lib.orc_max_threads.restype = ctypes.c_int
+            _lib.orc_compass_groups.restype = ctypes.c_int
+            _lib.orc_compass_groups.argtypes = [P, P, P, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P, P,
+                                                P, ctypes.c_float, P, P, P, P, P, P, P, P, P, ctypes.c_int]
             _lib.orc_kick_at.restype = ctypes.c_float
             _lib.orc_kick_at.argtypes = [P, ctypes.c_float, ctypes.c_float]
             _lib.orc_align_chi2.restype = ctypes.c_int
@@ -423,3 +426,38 @@ def decode_groups(raw, ev_off, n_events, gg, n_threads=0):
     goff[1:] = np.cumsum(counts)
     return GroupHits(x[order], z[order], yb[order], ye[order], w[order], h.id[:n][order],
                      goff.astype(np.uint32), order.astype(np.int64))
+
+
+def compass_groups(gh, batch, params, tol_y=10.0, kick_map=None, n_threads=0):
+    """Compass on the sector-group layout (row f2; orc_compass_groups):
+    windows over groups with y windows by two binary searches, then the
+    same tracklet search and selection.  gh: GroupHits of decode_groups;
+    batch: synth.grouped.GroupedBatch (its VELO tracks).  Hit indices refer
+    to gh's output order."""
+    gg = batch.geom
+    E = batch.n_events
+    T = int(batch.trk_off[E])
+    geo = geom_struct(gg.base)
+    pp = params_struct(params, kick_map)
+    edges = np.ascontiguousarray(gg.group_edges(), np.float32)
+    v = [np.ascontiguousarray(a[:T], np.float32) for a in (batch.velo_x, batch.velo_y, batch.velo_tx, batch.velo_ty)]
+    vfl = np.ascontiguousarray(batch.velo_flags[:T], np.uint8)
+    toff = np.ascontiguousarray(batch.trk_off[: E + 1], np.uint32)
+    Tn = max(T, 1)
+    out = Tracks(np.full((Tn, 4), -1, np.int32), np.zeros(Tn, np.float32), np.zeros(Tn, np.float32),
+                 np.zeros(Tn, np.float32), np.zeros(Tn, np.float32), np.zeros(Tn, np.uint8), np.zeros(Tn, np.uint8),
+                 None, np.zeros(Tn, np.float64), np.zeros(Tn, np.float64), np.zeros(Tn, np.float64))
+    gx = np.ascontiguousarray(gh.x, np.float32)
+    gyb = np.ascontiguousarray(gh.y_begin, np.float32)
+    gye = np.ascontiguousarray(gh.y_end, np.float32)
+    goff = np.ascontiguousarray(gh.group_off, np.uint32)
+    rc = lib().orc_compass_groups(_p(gx), _p(gyb), _p(gye), _p(goff), E, ctypes.byref(geo), int(gg.n_groups),
+                                  _p(edges), _p(v[0]), _p(v[1]), _p(v[2]), _p(v[3]), _p(vfl), _p(toff),
+                                  ctypes.byref(pp), float(tol_y), _p(out.hit), _p(out.qop), _p(out.chi2),
+                                  _p(out.x), _p(out.tx), _p(out.nhits), _p(out.found), _p(out.near),
+                                  _p(out.qop64), n_threads)
+    if rc != 0:
+        raise OracleError(rc, -1)
+    if T == 0:
+        out = Tracks(*(a[:0] if isinstance(a, np.ndarray) else a for a in dataclasses.astuple(out)))
+    return out

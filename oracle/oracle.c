@@ -725,6 +725,137 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
 }
 
 /*
+ * Compass on the sector-group layout (Sec. V-A with the groups of Sec. IV,
+ * row f2): per track and layer, the groups searched are the one holding
+ * the prediction u (the count of interior group edges <= u) and its
+ * neighbours in the slot order c, c-1, c+1, c-2, c+2 (n_sectors of them,
+ * inside the plane); inside a group (hits sorted by yBegin, yEnd = yBegin +
+ * height) the y window is found by two binary searches -- the first hit
+ * with yEnd >= y - tol_y and the first with yBegin > y + tol_y, y the
+ * track's y at the plane, (float)((double)vy + (double)vty dz) -- and the
+ * hits of the y window are refined by the x window |d| <= hw as in
+ * orc_compass.  The candidates of a layer are those hits in slot order,
+ * then y-window order; the tracklet search and selection are
+ * search_tracklets.  Hit indices refer to the group layout.  gx, gyb, gye:
+ * x at y = 0, yBegin, yEnd in output order; group_off[E * 4 * n_groups + 1];
+ * g: the plane's columns (S = columns, pitch, x_min).  The kick map of the
+ * params applies as in orc_compass.
+ */
+int orc_compass_groups(const float* gx, const float* gyb, const float* gye, const uint32_t* group_off, int E,
+                       const orc_geom* g, int n_groups, const float* edges, const float* vx, const float* vy,
+                       const float* vtx, const float* vty, const uint8_t* vflags, const uint32_t* trk_off,
+                       const orc_params* p, float tol_y, int32_t* hit, float* qop, float* chi2, float* xo,
+                       float* txo, uint8_t* nhits, uint8_t* found, double* near_m, double* qop64, int n_threads) {
+    set_threads(n_threads);
+    const int nsec = p->n_sectors, NG = n_groups;
+    if (nsec < 1 || nsec > 5 || p->n_candidates < 1 || NG < 1 || p->gec_max_hits < 0) return ORC_ERR_ARG;
+    static const int slot_off[5] = {0, -1, 1, -2, 2};
+    const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
+    const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
+    const float ptx = 1.0f / (p->sigma_tx_prior * p->sigma_tx_prior);
+    float t[4], f[4], hw[4];
+    const float kq = p->kick_k * p->qop_max;
+    for (int l = 0; l < 4; ++l) {
+        t[l] = g->z[l] - g->z_velo;
+        f[l] = p->kick_k * (g->z[l] - p->z_kink);
+        hw[l] = kq * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+    }
+    const float slope_tol = kq + p->tol_slope;
+    const double x_max = (double)g->x_min + (double)g->S * (double)g->pitch;
+
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int e = 0; e < E; ++e) {
+        range_t R[4] = {{0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}};
+        float* dv[4] = {NULL, NULL, NULL, NULL};
+        int dcap[4] = {0, 0, 0, 0};
+        const uint32_t ev_hits = group_off[(size_t)(e + 1) * 4 * NG] - group_off[(size_t)e * 4 * NG];
+        const int cut = p->gec_max_hits > 0 && ev_hits > (uint32_t)p->gec_max_hits;
+        for (uint32_t tr = trk_off[e]; tr < trk_off[e + 1]; ++tr) {
+            double mm = INFINITY;
+            for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = -1;
+            qop[tr] = 0.f; chi2[tr] = 0.f; xo[tr] = vx[tr]; txo[tr] = vtx[tr];
+            nhits[tr] = 0; found[tr] = 0; qop64[tr] = 0.0;
+            if (cut || (vflags[tr] & 1u)) { near_m[tr] = mm; continue; }
+            double u[4];
+            float uhi[4], ulo[4];
+            extrapolate(g, vx[tr], vy[tr], vtx[tr], vty[tr], u, uhi, ulo);
+            if (!(u[0] >= (double)g->x_min && u[0] <= x_max)) { near_m[tr] = mm; continue; }
+            float hwt[4], stol = slope_tol, kick = p->kick_k;
+            for (int l = 0; l < 4; ++l) hwt[l] = hw[l];
+            if (p->kmap_nx) {
+                kick = kick_at(p, vtx[tr], vty[tr]);
+                const float kqt = kick * p->qop_max;
+                for (int l = 0; l < 4; ++l) hwt[l] = kqt * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+                stol = kqt + p->tol_slope;
+            }
+            int any = 0;
+            for (int l = 0; l < 4; ++l) {
+                R[l].n = 0;
+                const double dz = (double)g->z[l] - (double)g->z_velo;
+                const float y = (float)((double)vy[tr] + (double)vty[tr] * dz);
+                const float ylo = y - tol_y, yhi = y + tol_y;
+                int c = 0;
+                for (int k = 1; k < NG; ++k) if ((double)edges[k] <= u[l]) c = k;
+                for (int k = 0; k < nsec; ++k) {
+                    const int grp = c + slot_off[k];
+                    if (grp < 0 || grp >= NG) continue;
+                    const size_t cell = ((size_t)e * 4 + (size_t)l) * (size_t)NG + (size_t)grp;
+                    uint32_t a = group_off[cell], b = group_off[cell + 1];
+                    /* first hit with yEnd >= ylo */
+                    uint32_t lo = a, hi = b;
+                    while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gye[m] >= ylo) hi = m; else lo = m + 1; }
+                    const uint32_t j0 = lo;
+                    /* first hit with yBegin > yhi */
+                    lo = j0; hi = b;
+                    while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gyb[m] > yhi) hi = m; else lo = m + 1; }
+                    const uint32_t j1 = lo;
+                    for (uint32_t j = j0; j < j1; ++j) {
+                        const float dj = (gx[j] - uhi[l]) - ulo[l];
+                        double ma = margin(dj, -hwt[l]), mb = margin(dj, hwt[l]);
+                        if (ma < mm) mm = ma;
+                        if (mb < mm) mm = mb;
+                        if (dj >= -hwt[l] && dj <= hwt[l]) { range_push(&R[l], j); any = 1; }
+                    }
+                }
+                if (dcap[l] < R[l].n) {
+                    dcap[l] = R[l].n;
+                    dv[l] = (float*)realloc(dv[l], (size_t)dcap[l] * sizeof(float));
+                }
+                for (int i = 0; i < R[l].n; ++i) dv[l][i] = (gx[R[l].idx[i]] - uhi[l]) - ulo[l];
+            }
+            if (!any) { near_m[tr] = mm; continue; }
+            int best_n = 0;
+            float best_chi2 = 0.f, best_q = 0.f, best_a = 0.f, best_b = 0.f;
+            int32_t best_hit[4] = {-1, -1, -1, -1};
+            search_tracklets(g, p, R, dv, t, f, w, px, ptx, stol, &mm, &best_n, &best_chi2, &best_q, &best_a,
+                             &best_b, best_hit);
+            near_m[tr] = mm;
+            if (best_n == 0) continue;
+            for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = best_hit[l];
+            qop[tr] = p->kmap_nx ? best_q * (p->kick_k / kick) : best_q;
+            chi2[tr] = best_chi2;
+            xo[tr] = vx[tr] + best_a;
+            txo[tr] = vtx[tr] + best_b;
+            nhits[tr] = (uint8_t)best_n;
+            found[tr] = 1;
+            double d64[4] = {0, 0, 0, 0}, t64[4], f64[4], delta[3], c64;
+            int pr[4];
+            for (int l = 0; l < 4; ++l) {
+                pr[l] = best_hit[l] >= 0;
+                t64[l] = (double)g->z[l] - (double)g->z_velo;
+                f64[l] = (double)p->kick_k * ((double)g->z[l] - (double)p->z_kink);
+                if (pr[l]) d64[l] = (double)gx[best_hit[l]] - u[l];
+            }
+            double sh = (double)p->sigma_hit, sx = (double)p->sigma_x_prior, st = (double)p->sigma_tx_prior;
+            if (orc_fit64_d(d64, pr, t64, f64, 1.0 / (sh * sh), 1.0 / (sx * sx), 1.0 / (st * st), delta, &c64))
+                qop64[tr] = p->kmap_nx ? delta[2] * ((double)p->kick_k / (double)kick) : delta[2];
+        }
+        for (int l = 0; l < 4; ++l) { free(R[l].idx); free(dv[l]); }
+    }
+    return ORC_OK;
+}
+
+/*
  * Standalone fit of given hits (the refit step): for each track, hits
  * hit[T*4] (-1 = absent) are fitted in float (same arithmetic as the
  * search) and in double.  Outputs per track: q/p, chi2, x, tx (float) and

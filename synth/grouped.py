@@ -32,6 +32,7 @@ class GroupGeometry:
     sensor_height: float = 250.0
     n_groups: int = 24
     base: Geometry = None
+    edges: np.ndarray = None    # optional explicit group edges (float32[n_groups + 1])
 
     def __post_init__(self):
         if self.base is None:
@@ -51,6 +52,8 @@ class GroupGeometry:
 
     def group_edges(self) -> np.ndarray:
         """float32[n_groups + 1]: x edges of the groups (x_min ... x_max)."""
+        if self.edges is not None:
+            return np.asarray(self.edges, np.float32)
         half = self.n_groups // 2
         span = self.n_columns * SECTOR_PITCH / 2.0
         w0 = span / (half * (half + 1) / 2.0)
@@ -79,12 +82,24 @@ class GroupedBatch:
     truth_flags: np.ndarray
     truth_track: np.ndarray
     truth_y: np.ndarray         # float64: the track's y at the plane (NaN for noise)
+    velo_x: np.ndarray = None   # the VELO tracks of the base batch (as synth.Batch)
+    velo_y: np.ndarray = None
+    velo_tx: np.ndarray = None
+    velo_ty: np.ndarray = None
+    velo_flags: np.ndarray = None
+    trk_off: np.ndarray = None
+    qop_true: np.ndarray = None
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.trk_off[-1])
 
 
 def generate_grouped(n_events: int, n_columns: int = 16, rows: int = 4, sensor_height: float = 250.0,
-                     n_groups: int = 24, tracks=60, hits=1200, seed: int = 1) -> GroupedBatch:
-    gg = GroupGeometry(n_columns, rows, sensor_height, n_groups)
-    b = generate(n_events=n_events, n_sectors=n_columns, tracks=tracks, hits=hits, seed=seed)
+                     n_groups: int = 24, tracks=60, hits=1200, seed: int = 1, edges=None, **kw) -> GroupedBatch:
+    """kw: further arguments of the base generator (noise_frac, efficiency, ...)."""
+    gg = GroupGeometry(n_columns, rows, sensor_height, n_groups, edges=edges)
+    b = generate(n_events=n_events, n_sectors=n_columns, tracks=tracks, hits=hits, seed=seed, **kw)
     rng = np.random.Generator(np.random.Philox(key=seed + 7919))
     tr = b.truth_track
     sig = tr >= 0
@@ -110,4 +125,5 @@ def generate_grouped(n_events: int, n_columns: int = 16, rows: int = 4, sensor_h
     raw, ev_off = encode(bank_n.reshape(n_events, B), hv, fl, S2)
     return GroupedBatch(gg, n_events, raw, ev_off, bank_n.astype(np.uint32), ev.astype(np.int32),
                         ly.astype(np.int8), col.astype(np.int16), rw.astype(np.int16), hv.astype(np.int16),
-                        fl.astype(np.int8), trk.astype(np.int64), yy)
+                        fl.astype(np.int8), trk.astype(np.int64), yy, b.velo_x, b.velo_y, b.velo_tx, b.velo_ty,
+                        b.velo_flags, b.trk_off, b.qop_true)

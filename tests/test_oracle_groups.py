@@ -77,3 +77,56 @@ def test_event_offsets_match_the_banks():
     per_event = b.bank_n.reshape(b.n_events, g.n_banks).sum(axis=1)
     assert np.array_equal(np.diff(gh.group_off[np.arange(0, b.n_events * 4 * g.n_groups + 1, 4 * g.n_groups)]),
                           per_event)
+
+
+def _column_edges(S):
+    x_min = -S * 96.0 / 2.0
+    return (x_min + 96.0 * np.arange(S + 1)).astype(np.float32)
+
+
+def test_group_search_reduces_to_the_sector_search():
+    """One row of sensors taller than the tracks' y range, one group per
+    column, no y cut and no candidate limit: the group search is the sector
+    search of orc_compass on the same raw banks (the candidate order inside
+    a window differs, which without a candidate limit only matters for exact
+    ties: compared by hit position)."""
+    import synth
+    S = 16
+    kw = dict(n_events=10, tracks=60, hits=900, seed=31)
+    gb = generate_grouped(n_columns=S, rows=1, sensor_height=10000.0, n_groups=S, edges=_column_edges(S), **kw)
+    b0 = synth.generate(n_sectors=S, **kw)
+    assert np.array_equal(gb.raw, b0.raw)
+    P = synth.CompassParams().replace(n_candidates=100000)
+    hits, base = oracle.run_batch(b0, P)
+    gh = oracle.decode_groups(gb.raw, gb.ev_off, gb.n_events, gb.geom)
+    grp = oracle.compass_groups(gh, gb, P, tol_y=1e6)
+    assert np.array_equal(grp.found, base.found) and np.array_equal(grp.nhits, base.nhits)
+    assert int(base.found.sum()) > 300
+    m = base.hit >= 0
+    assert np.array_equal(grp.hit >= 0, m)
+    assert np.array_equal(gh.x[grp.hit[m]].view(np.uint32), hits.x[base.hit[m]].view(np.uint32))
+    for k in ("qop", "chi2", "x", "tx"):
+        assert np.array_equal(getattr(grp, k).view(np.uint32), getattr(base, k).view(np.uint32)), k
+
+
+def test_y_windows_reject_the_other_rows():
+    """With sensor rows, hits of the other rows in the searched groups are
+    outside a track's y window (the track's y at the plane lies in its own
+    strips' range): against the same search without a y cut, more found
+    tracks carry their own particle's hits and far fewer are fakes; a y
+    window that admits nothing finds nothing."""
+    import synth
+    gb = generate_grouped(12, rows=4, n_groups=16, tracks=80, hits=2000, seed=33)
+    gh = oracle.decode_groups(gb.raw, gb.ev_off, gb.n_events, gb.geom)
+    P = synth.CompassParams()
+    owner = gb.truth_track[gh.src]
+
+    def score(t):
+        m = np.nonzero(t.found)[0]
+        good = sum(np.mean(owner[t.hit[tr][t.hit[tr] >= 0]] == tr) >= 0.7 for tr in m)
+        return good, len(m) - good
+
+    good_y, fake_y = score(oracle.compass_groups(gh, gb, P, tol_y=5.0))
+    good_n, fake_n = score(oracle.compass_groups(gh, gb, P, tol_y=1e6))
+    assert good_y > good_n and fake_y < 0.2 * fake_n
+    assert not oracle.compass_groups(gh, gb, P, tol_y=-1e6).found.any()
