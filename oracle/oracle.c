@@ -27,10 +27,15 @@
  *                  (kick_at) in place of the constant kick
  *   Sec. V-C       CPU form: windows computed per track right before the
  *                  tracklet search, OpenMP over events
+ *   Sec. IV, V-A   sector groups: the search over x regions with y windows
+ *                  (orc_compass_groups); the group layout itself is written
+ *                  out in oracle/__init__.py (decode_groups)
  *
  * Parity status: decode, sort and offsets are pinned (round trip, closed
  * form, brute force).  The Compass search is pinned by a brute-force search
- * and by isolated-track recovery; the fits by closed forms.  Selections
+ * and by isolated-track recovery; the fits by closed forms; the kick map by
+ * closed forms and the generator's field; the group search by its reduction
+ * to the sector search.  Selections
  * against generator truth are reported, not pinned (parity unpinned there:
  * the paper's numbers are on LHCb samples that are not available).
  */
