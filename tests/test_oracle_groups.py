@@ -130,3 +130,26 @@ def test_y_windows_reject_the_other_rows():
     good_n, fake_n = score(oracle.compass_groups(gh, gb, P, tol_y=1e6))
     assert good_y > good_n and fake_y < 0.2 * fake_n
     assert not oracle.compass_groups(gh, gb, P, tol_y=-1e6).found.any()
+
+
+def test_group_search_event_cut_and_constant_kick_map():
+    """The Global Event Cut and the kick map act on the group search as on
+    the sector search: events above the cut find nothing, and a constant
+    map equal to kick_k changes nothing, bit for bit."""
+    import synth
+    gb = generate_grouped(10, rows=4, n_groups=16, tracks=60, hits=1500, seed=35)
+    gh = oracle.decode_groups(gb.raw, gb.ev_off, gb.n_events, gb.geom)
+    P = synth.CompassParams()
+    base = oracle.compass_groups(gh, gb, P, tol_y=5.0)
+    per_event = np.diff(gh.group_off[:: 4 * gb.geom.n_groups].astype(np.int64))
+    cutp = P.replace(gec_max_hits=int(np.median(per_event)))
+    cut = oracle.compass_groups(gh, gb, cutp, tol_y=5.0)
+    over = np.repeat(per_event > cutp.gec_max_hits, np.diff(gb.trk_off.astype(np.int64)))
+    assert over.any() and (~over).any()
+    assert not cut.found[over].any()
+    assert np.array_equal(cut.hit[~over], base.hit[~over])
+    km = synth.KickMap(2, 2, 0.3, 0.25, np.full((2, 2), P.kick_k, np.float32))
+    same = oracle.compass_groups(gh, gb, P, tol_y=5.0, kick_map=km)
+    assert np.array_equal(same.hit, base.hit)
+    for k in ("qop", "chi2", "x", "tx"):
+        assert np.array_equal(getattr(same, k).view(np.uint32), getattr(base, k).view(np.uint32)), k
