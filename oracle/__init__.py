@@ -80,6 +80,9 @@ def lib():
             _lib.orc_compass_groups.restype = ctypes.c_int
             _lib.orc_compass_groups.argtypes = [P, P, P, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P, P,
                                                 P, ctypes.c_float, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+            _lib.orc_group_candidates.restype = ctypes.c_int
+            _lib.orc_group_candidates.argtypes = [P, P, P, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P, P,
+                                                  P, ctypes.c_float, ctypes.c_int, P, P]
             _lib.orc_kick_at.restype = ctypes.c_float
             _lib.orc_kick_at.argtypes = [P, ctypes.c_float, ctypes.c_float]
             _lib.orc_align_chi2.restype = ctypes.c_int
@@ -428,19 +431,21 @@ def decode_groups(raw, ev_off, n_events, gg, n_threads=0):
                      goff.astype(np.uint32), order.astype(np.int64))
 
 
-def compass_groups(gh, batch, params, tol_y=10.0, kick_map=None, n_threads=0):
+def compass_groups(gh, batch, params, tol_y=10.0, kick_map=None, n_threads=0, vy=None, vty=None):
     """Compass on the sector-group layout (row f2; orc_compass_groups):
     windows over groups with y windows by two binary searches, then the
     same tracklet search and selection.  gh: GroupHits of decode_groups;
-    batch: synth.grouped.GroupedBatch (its VELO tracks).  Hit indices refer
-    to gh's output order."""
+    batch: synth.grouped.GroupedBatch (its VELO tracks; vy, vty optionally
+    replace their y and ty).  Hit indices refer to gh's output order."""
     gg = batch.geom
     E = batch.n_events
     T = int(batch.trk_off[E])
     geo = geom_struct(gg.base)
     pp = params_struct(params, kick_map)
     edges = np.ascontiguousarray(gg.group_edges(), np.float32)
-    v = [np.ascontiguousarray(a[:T], np.float32) for a in (batch.velo_x, batch.velo_y, batch.velo_tx, batch.velo_ty)]
+    vy = batch.velo_y if vy is None else vy
+    vty = batch.velo_ty if vty is None else vty
+    v = [np.ascontiguousarray(a[:T], np.float32) for a in (batch.velo_x, vy, batch.velo_tx, vty)]
     vfl = np.ascontiguousarray(batch.velo_flags[:T], np.uint8)
     toff = np.ascontiguousarray(batch.trk_off[: E + 1], np.uint32)
     Tn = max(T, 1)
@@ -461,3 +466,32 @@ def compass_groups(gh, batch, params, tol_y=10.0, kick_map=None, n_threads=0):
     if T == 0:
         out = Tracks(*(a[:0] if isinstance(a, np.ndarray) else a for a in dataclasses.astuple(out)))
     return out
+
+
+def group_candidates(gh, batch, params, tol_y=10.0, kick_map=None, max_cand=4096, vy=None, vty=None):
+    """The candidates of every track of the group search
+    (orc_group_candidates): int32 [T, 4, max_cand] group-layout indices in
+    the search's order and int32 [T, 4] counts.  vy, vty (optional) replace
+    the batch's VELO y and ty."""
+    gg = batch.geom
+    E = batch.n_events
+    T = int(batch.trk_off[E])
+    geo = geom_struct(gg.base)
+    pp = params_struct(params, kick_map)
+    edges = np.ascontiguousarray(gg.group_edges(), np.float32)
+    vy = batch.velo_y if vy is None else vy
+    vty = batch.velo_ty if vty is None else vty
+    v = [np.ascontiguousarray(a[:T], np.float32) for a in (batch.velo_x, vy, batch.velo_tx, vty)]
+    vfl = np.ascontiguousarray(batch.velo_flags[:T], np.uint8)
+    toff = np.ascontiguousarray(batch.trk_off[: E + 1], np.uint32)
+    cand = np.full((max(T, 1), 4, max_cand), -1, np.int32)
+    n = np.zeros((max(T, 1), 4), np.int32)
+    rc = lib().orc_group_candidates(_p(np.ascontiguousarray(gh.x, np.float32)),
+                                    _p(np.ascontiguousarray(gh.y_begin, np.float32)),
+                                    _p(np.ascontiguousarray(gh.y_end, np.float32)),
+                                    _p(np.ascontiguousarray(gh.group_off, np.uint32)), E, ctypes.byref(geo),
+                                    int(gg.n_groups), _p(edges), _p(v[0]), _p(v[1]), _p(v[2]), _p(v[3]), _p(vfl),
+                                    _p(toff), ctypes.byref(pp), float(tol_y), int(max_cand), _p(cand), _p(n))
+    if rc != 0:
+        raise OracleError(rc, -1)
+    return cand[:T], n[:T]

@@ -35,7 +35,9 @@
  * form, brute force).  The Compass search is pinned by a brute-force search
  * and by isolated-track recovery; the fits by closed forms; the kick map by
  * closed forms and the generator's field; the group search by its reduction
- * to the sector search.  Selections
+ * to the sector search, and its candidate windows (group choice, both y
+ * cuts with exact ties, the x cut) by a scan of every hit of the searched
+ * groups.  Selections
  * against generator truth are reported, not pinned (parity unpinned there:
  * the paper's numbers are on LHCb samples that are not available).
  */
@@ -730,21 +732,132 @@ int orc_compass(const float* hx, const uint32_t* hit_off, int E, const orc_geom*
 }
 
 /*
+ * Candidate hits of one track on the sector-group layout (Sec. V-A with the
+ * groups of Sec. IV, row f2).  Per layer l:
+ *   - the groups searched: the one holding the prediction u_l (the number
+ *     of interior group edges <= u_l, compared in double) and its
+ *     neighbours in the slot order c, c-1, c+1, c-2, c+2 (n_sectors of
+ *     them, inside the plane);
+ *   - inside a group (hits sorted by yBegin), the y window by two binary
+ *     searches: j0 = first hit with yEnd >= ylo, then j1 = first hit at or
+ *     after j0 with yBegin > yhi, where y = (float)(vy + vty (z_l - z_velo))
+ *     in double, ylo = y - tol_y and yhi = y + tol_y in float.  The first
+ *     search needs yEnd non-decreasing inside the group too: it is when
+ *     every sensor has the same height (yEnd = yBegin + height, and float
+ *     addition is monotone); orc_compass_groups checks it.  A hit of the
+ *     group is then in the y window exactly when yEnd >= ylo and yBegin <= yhi;
+ *   - the hits of the y window refined by the x window |d| <= hw_l,
+ *     d = (x - uhi) - ulo.
+ * Candidates are listed in slot order, then y-window (storage) order; their
+ * residuals d go to dv[l].  *mm is lowered to the smallest relative margin
+ * of every decision taken: the group choice (u_l against the edges next to
+ * it), the two y cuts (the hits on either side of j0 and of j1: with both
+ * y columns monotone these are the nearest to each cut) and the x window.
+ * Returns whether some layer has a candidate.
+ */
+static int group_candidates(const float* gx, const float* gyb, const float* gye, const uint32_t* group_off,
+                            int e, int NG, const float* edges, int nsec, float tol_y, const orc_geom* g,
+                            float vy, float vty, const double* u, const float* uhi, const float* ulo,
+                            const float* hwt, range_t* R, float** dv, int* dcap, double* mm_io) {
+    static const int slot_off[5] = {0, -1, 1, -2, 2};
+    double mm = *mm_io;
+    int any = 0;
+    for (int l = 0; l < 4; ++l) {
+        R[l].n = 0;
+        const double dz = (double)g->z[l] - (double)g->z_velo;
+        const float y = (float)((double)vy + (double)vty * dz);
+        const float ylo = y - tol_y, yhi = y + tol_y;
+        int c = 0;
+        for (int k = 1; k < NG; ++k) if ((double)edges[k] <= u[l]) c = k;
+        for (int k = 1; k < NG; ++k) {  /* the group choice: margins to the interior edges around u */
+            if (k != c && k != c + 1) continue;
+            const double m = margin(u[l], (double)edges[k]);
+            if (m < mm) mm = m;
+        }
+        for (int k = 0; k < nsec; ++k) {
+            const int grp = c + slot_off[k];
+            if (grp < 0 || grp >= NG) continue;
+            const size_t cell = ((size_t)e * 4 + (size_t)l) * (size_t)NG + (size_t)grp;
+            const uint32_t a = group_off[cell], b = group_off[cell + 1];
+            /* first hit with yEnd >= ylo */
+            uint32_t lo = a, hi = b;
+            while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gye[m] >= ylo) hi = m; else lo = m + 1; }
+            const uint32_t j0 = lo;
+            /* first hit at or after j0 with yBegin > yhi */
+            lo = j0; hi = b;
+            while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gyb[m] > yhi) hi = m; else lo = m + 1; }
+            const uint32_t j1 = lo;
+            double m;
+            if (j0 > a) { m = margin(gye[j0 - 1], ylo); if (m < mm) mm = m; }
+            if (j0 < b) { m = margin(gye[j0], ylo); if (m < mm) mm = m; }
+            if (j1 > j0) { m = margin(gyb[j1 - 1], yhi); if (m < mm) mm = m; }
+            if (j1 < b) { m = margin(gyb[j1], yhi); if (m < mm) mm = m; }
+            for (uint32_t j = j0; j < j1; ++j) {
+                const float dj = (gx[j] - uhi[l]) - ulo[l];
+                double ma = margin(dj, -hwt[l]), mb = margin(dj, hwt[l]);
+                if (ma < mm) mm = ma;
+                if (mb < mm) mm = mb;
+                if (dj >= -hwt[l] && dj <= hwt[l]) { range_push(&R[l], j); any = 1; }
+            }
+        }
+        if (dcap[l] < R[l].n) {
+            dcap[l] = R[l].n;
+            dv[l] = (float*)realloc(dv[l], (size_t)dcap[l] * sizeof(float));
+        }
+        for (int i = 0; i < R[l].n; ++i) dv[l][i] = (gx[R[l].idx[i]] - uhi[l]) - ulo[l];
+    }
+    *mm_io = mm;
+    return any;
+}
+
+/* yBegin and yEnd non-decreasing inside every group of the E events (the
+ * two binary searches of group_candidates rely on it). */
+static int groups_y_sorted(const float* gyb, const float* gye, const uint32_t* group_off, int E, int NG) {
+    const size_t cells = (size_t)E * 4 * (size_t)NG;
+    for (size_t c = 0; c < cells; ++c)
+        for (uint32_t j = group_off[c] + 1; j < group_off[c + 1]; ++j)
+            if (gyb[j] < gyb[j - 1] || gye[j] < gye[j - 1]) return 0;
+    return 1;
+}
+
+/* Per-track part shared by the group search and its candidate listing:
+ * the track's kick (map or constant), its window half-widths and slope cut,
+ * the extrapolation, and the acceptance (not backward, u_0 inside the
+ * plane; its margins lower *mm).  Returns whether the track is searched. */
+static int group_track_setup(const orc_geom* g, const orc_params* p, float vx, float vy, float vtx, float vty,
+                             uint8_t vflags, const float* hw, float slope_tol, double* u, float* uhi, float* ulo,
+                             float* hwt, float* stol, float* kick, double* mm) {
+    *stol = slope_tol;
+    *kick = p->kick_k;
+    for (int l = 0; l < 4; ++l) hwt[l] = hw[l];
+    if (vflags & 1u) return 0;
+    extrapolate(g, vx, vy, vtx, vty, u, uhi, ulo);
+    const double x_max = (double)g->x_min + (double)g->S * (double)g->pitch;
+    const double m0 = margin(u[0], (double)g->x_min), m1 = margin(u[0], x_max);
+    if (m0 < *mm) *mm = m0;
+    if (m1 < *mm) *mm = m1;
+    if (!(u[0] >= (double)g->x_min && u[0] <= x_max)) return 0;
+    if (p->kmap_nx) {
+        *kick = kick_at(p, vtx, vty);
+        const float kqt = *kick * p->qop_max;
+        for (int l = 0; l < 4; ++l) hwt[l] = kqt * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+        *stol = kqt + p->tol_slope;
+    }
+    return 1;
+}
+
+/*
  * Compass on the sector-group layout (Sec. V-A with the groups of Sec. IV,
- * row f2): per track and layer, the groups searched are the one holding
- * the prediction u (the count of interior group edges <= u) and its
- * neighbours in the slot order c, c-1, c+1, c-2, c+2 (n_sectors of them,
- * inside the plane); inside a group (hits sorted by yBegin, yEnd = yBegin +
- * height) the y window is found by two binary searches -- the first hit
- * with yEnd >= y - tol_y and the first with yBegin > y + tol_y, y the
- * track's y at the plane, (float)((double)vy + (double)vty dz) -- and the
- * hits of the y window are refined by the x window |d| <= hw as in
- * orc_compass.  The candidates of a layer are those hits in slot order,
- * then y-window order; the tracklet search and selection are
- * search_tracklets.  Hit indices refer to the group layout.  gx, gyb, gye:
- * x at y = 0, yBegin, yEnd in output order; group_off[E * 4 * n_groups + 1];
- * g: the plane's columns (S = columns, pitch, x_min).  The kick map of the
- * params applies as in orc_compass.
+ * row f2): per track, its candidates (group_candidates: groups around the
+ * prediction, y windows by two binary searches, x windows), then the
+ * tracklet search and selection of the sector search (search_tracklets).
+ * Hit indices refer to the group layout.  gx, gyb, gye: x at y = 0,
+ * yBegin, yEnd in output order; group_off[E * 4 * n_groups + 1]; g: the
+ * plane's columns (S = columns, pitch, x_min).  The kick map and the Global
+ * Event Cut of the params apply as in orc_compass.  near_m: the smallest
+ * decision margin of each track (acceptance, group choice, y and x windows,
+ * pair cuts, collection, chi2 cut and ordering).  Returns ORC_ERR_ARG when
+ * yBegin or yEnd decreases inside a group (sensors of different heights).
  */
 int orc_compass_groups(const float* gx, const float* gyb, const float* gye, const uint32_t* group_off, int E,
                        const orc_geom* g, int n_groups, const float* edges, const float* vx, const float* vy,
@@ -754,7 +867,7 @@ int orc_compass_groups(const float* gx, const float* gyb, const float* gye, cons
     set_threads(n_threads);
     const int nsec = p->n_sectors, NG = n_groups;
     if (nsec < 1 || nsec > 5 || p->n_candidates < 1 || NG < 1 || p->gec_max_hits < 0) return ORC_ERR_ARG;
-    static const int slot_off[5] = {0, -1, 1, -2, 2};
+    if (!groups_y_sorted(gyb, gye, group_off, E, NG)) return ORC_ERR_ARG;
     const float w = 1.0f / (p->sigma_hit * p->sigma_hit);
     const float px = 1.0f / (p->sigma_x_prior * p->sigma_x_prior);
     const float ptx = 1.0f / (p->sigma_tx_prior * p->sigma_tx_prior);
@@ -766,7 +879,6 @@ int orc_compass_groups(const float* gx, const float* gyb, const float* gye, cons
         hw[l] = kq * fabsf(g->z[l] - p->z_kink) + p->tol_win;
     }
     const float slope_tol = kq + p->tol_slope;
-    const double x_max = (double)g->x_min + (double)g->S * (double)g->pitch;
 
 #pragma omp parallel for schedule(dynamic, 2)
     for (int e = 0; e < E; ++e) {
@@ -780,55 +892,18 @@ int orc_compass_groups(const float* gx, const float* gyb, const float* gye, cons
             for (int l = 0; l < 4; ++l) hit[(size_t)tr * 4 + l] = -1;
             qop[tr] = 0.f; chi2[tr] = 0.f; xo[tr] = vx[tr]; txo[tr] = vtx[tr];
             nhits[tr] = 0; found[tr] = 0; qop64[tr] = 0.0;
-            if (cut || (vflags[tr] & 1u)) { near_m[tr] = mm; continue; }
             double u[4];
-            float uhi[4], ulo[4];
-            extrapolate(g, vx[tr], vy[tr], vtx[tr], vty[tr], u, uhi, ulo);
-            if (!(u[0] >= (double)g->x_min && u[0] <= x_max)) { near_m[tr] = mm; continue; }
-            float hwt[4], stol = slope_tol, kick = p->kick_k;
-            for (int l = 0; l < 4; ++l) hwt[l] = hw[l];
-            if (p->kmap_nx) {
-                kick = kick_at(p, vtx[tr], vty[tr]);
-                const float kqt = kick * p->qop_max;
-                for (int l = 0; l < 4; ++l) hwt[l] = kqt * fabsf(g->z[l] - p->z_kink) + p->tol_win;
-                stol = kqt + p->tol_slope;
+            float uhi[4], ulo[4], hwt[4], stol, kick;
+            if (cut || !group_track_setup(g, p, vx[tr], vy[tr], vtx[tr], vty[tr], vflags[tr], hw, slope_tol, u, uhi,
+                                          ulo, hwt, &stol, &kick, &mm)) {
+                near_m[tr] = mm;
+                continue;
             }
-            int any = 0;
-            for (int l = 0; l < 4; ++l) {
-                R[l].n = 0;
-                const double dz = (double)g->z[l] - (double)g->z_velo;
-                const float y = (float)((double)vy[tr] + (double)vty[tr] * dz);
-                const float ylo = y - tol_y, yhi = y + tol_y;
-                int c = 0;
-                for (int k = 1; k < NG; ++k) if ((double)edges[k] <= u[l]) c = k;
-                for (int k = 0; k < nsec; ++k) {
-                    const int grp = c + slot_off[k];
-                    if (grp < 0 || grp >= NG) continue;
-                    const size_t cell = ((size_t)e * 4 + (size_t)l) * (size_t)NG + (size_t)grp;
-                    uint32_t a = group_off[cell], b = group_off[cell + 1];
-                    /* first hit with yEnd >= ylo */
-                    uint32_t lo = a, hi = b;
-                    while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gye[m] >= ylo) hi = m; else lo = m + 1; }
-                    const uint32_t j0 = lo;
-                    /* first hit with yBegin > yhi */
-                    lo = j0; hi = b;
-                    while (lo < hi) { uint32_t m = lo + (hi - lo) / 2; if (gyb[m] > yhi) hi = m; else lo = m + 1; }
-                    const uint32_t j1 = lo;
-                    for (uint32_t j = j0; j < j1; ++j) {
-                        const float dj = (gx[j] - uhi[l]) - ulo[l];
-                        double ma = margin(dj, -hwt[l]), mb = margin(dj, hwt[l]);
-                        if (ma < mm) mm = ma;
-                        if (mb < mm) mm = mb;
-                        if (dj >= -hwt[l] && dj <= hwt[l]) { range_push(&R[l], j); any = 1; }
-                    }
-                }
-                if (dcap[l] < R[l].n) {
-                    dcap[l] = R[l].n;
-                    dv[l] = (float*)realloc(dv[l], (size_t)dcap[l] * sizeof(float));
-                }
-                for (int i = 0; i < R[l].n; ++i) dv[l][i] = (gx[R[l].idx[i]] - uhi[l]) - ulo[l];
+            if (!group_candidates(gx, gyb, gye, group_off, e, NG, edges, nsec, tol_y, g, vy[tr], vty[tr], u, uhi,
+                                  ulo, hwt, R, dv, dcap, &mm)) {
+                near_m[tr] = mm;
+                continue;
             }
-            if (!any) { near_m[tr] = mm; continue; }
             int best_n = 0;
             float best_chi2 = 0.f, best_q = 0.f, best_a = 0.f, best_b = 0.f;
             int32_t best_hit[4] = {-1, -1, -1, -1};
@@ -858,6 +933,49 @@ int orc_compass_groups(const float* gx, const float* gyb, const float* gye, cons
         for (int l = 0; l < 4; ++l) { free(R[l].idx); free(dv[l]); }
     }
     return ORC_OK;
+}
+
+/*
+ * The candidates of every track of the group search (exposed for tests):
+ * cand[(tr * 4 + l) * max_cand + i] = group-layout index of candidate i of
+ * layer l in the search's order, n_cand[tr * 4 + l] = their count (0 for
+ * a track that is not searched).  Returns ORC_ERR_CAPACITY if a list has
+ * more than max_cand entries, ORC_ERR_ARG as orc_compass_groups.
+ */
+int orc_group_candidates(const float* gx, const float* gyb, const float* gye, const uint32_t* group_off, int E,
+                         const orc_geom* g, int n_groups, const float* edges, const float* vx, const float* vy,
+                         const float* vtx, const float* vty, const uint8_t* vflags, const uint32_t* trk_off,
+                         const orc_params* p, float tol_y, int max_cand, int32_t* cand, int32_t* n_cand) {
+    const int nsec = p->n_sectors, NG = n_groups;
+    if (nsec < 1 || nsec > 5 || NG < 1 || max_cand < 0) return ORC_ERR_ARG;
+    if (!groups_y_sorted(gyb, gye, group_off, E, NG)) return ORC_ERR_ARG;
+    float hw[4];
+    const float kq = p->kick_k * p->qop_max;
+    for (int l = 0; l < 4; ++l) hw[l] = kq * fabsf(g->z[l] - p->z_kink) + p->tol_win;
+    const float slope_tol = kq + p->tol_slope;
+    int rc = ORC_OK;
+    range_t R[4] = {{0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}, {0, 0, NULL}};
+    float* dv[4] = {NULL, NULL, NULL, NULL};
+    int dcap[4] = {0, 0, 0, 0};
+    for (int e = 0; e < E; ++e) {
+        for (uint32_t tr = trk_off[e]; tr < trk_off[e + 1]; ++tr) {
+            double mm = INFINITY, u[4];
+            float uhi[4], ulo[4], hwt[4], stol, kick;
+            for (int l = 0; l < 4; ++l) { n_cand[(size_t)tr * 4 + l] = 0; R[l].n = 0; }
+            if (!group_track_setup(g, p, vx[tr], vy[tr], vtx[tr], vty[tr], vflags[tr], hw, slope_tol, u, uhi, ulo,
+                                   hwt, &stol, &kick, &mm))
+                continue;
+            group_candidates(gx, gyb, gye, group_off, e, NG, edges, nsec, tol_y, g, vy[tr], vty[tr], u, uhi, ulo,
+                             hwt, R, dv, dcap, &mm);
+            for (int l = 0; l < 4; ++l) {
+                if (R[l].n > max_cand) { rc = ORC_ERR_CAPACITY; continue; }
+                n_cand[(size_t)tr * 4 + l] = R[l].n;
+                for (int i = 0; i < R[l].n; ++i) cand[((size_t)tr * 4 + l) * (size_t)max_cand + i] = (int32_t)R[l].idx[i];
+            }
+        }
+    }
+    for (int l = 0; l < 4; ++l) { free(R[l].idx); free(dv[l]); }
+    return rc;
 }
 
 /*
