@@ -461,15 +461,17 @@ def measure_kick_map(g, params, cfg, reps=10):
     return res
 
 
-def measure_sector_groups(g, reps=10):
-    """ut_sector_groups (row f2, the sector-group hit layout) on 1000 events
-    of a detector with 48 columns x 4 rows of sensors per plane and 84
-    groups (200 tracks, 4000 hits per event): device time of the bank-order
-    decode and of the group pass (CUDA events, L2 flushed), and the group
-    pass's algorithmic bytes (id read, six 4-byte fields written per hit,
-    group offsets written) against the measured HBM bandwidth."""
+def measure_sector_groups(g, reps=10, tol_y=5.0):
+    """Row f2 on 1000 events of a detector with 48 columns x 4 rows of
+    sensors per plane and 84 groups (200 tracks, 4000 hits per event):
+    device time of the bank-order decode, of the group pass
+    (ut_sector_groups) and of the group search (compass_find_groups, y
+    windows of +-tol_y), CUDA events, L2 flushed; each pass's algorithmic
+    bytes against the measured HBM bandwidth (group pass: id read, six
+    4-byte fields written per hit, group offsets written)."""
     import numpy as np
     import torch
+    import synth
     from synth.grouped import generate_grouped
     b = generate_grouped(1000, n_columns=48, rows=4, n_groups=84, tracks=200, hits=4000, seed=21)
     gg = b.geom
@@ -481,30 +483,44 @@ def measure_sector_groups(g, reps=10):
     out = g.GroupHitBuffers.allocate(2 * nw + 8, E, gg.n_groups)
     ws = torch.empty((g.decode_workspace_size(E) + 15) // 16 * 4, dtype=torch.int32, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
-    t_dec, t_grp = [], []
+    velo = g.upload_velo(b)
+    tracks = g.TrackBuffers.allocate(b.n_tracks)
+    params = synth.CompassParams()
+    t_dec, t_grp, t_find = [], [], []
     for r in range(reps + 1):
         flush.add_(1)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record()
         g.ut_decode(ctx, raw_d, nw, ev_d, E, hits, False, ws)
         ev[1].record()
         g.ut_sector_groups(ctx, hits, E, gg, out)
         ev[2].record()
-        ev[2].synchronize()
+        g.compass_find_groups(ctx, out, gg, velo, E, params, tracks, tol_y)
+        ev[3].record()
+        ev[3].synchronize()
         if r:
             t_dec.append(ev[0].elapsed_time(ev[1]))
             t_grp.append(ev[1].elapsed_time(ev[2]))
+            t_find.append(ev[2].elapsed_time(ev[3]))
     ctx.check(what="sector groups")
     n = int(b.bank_n.sum())
+    T = b.n_tracks
     alg = n * (4 + 24) + (E * 4 * gg.n_groups + 1) * 4 + 2 * E * 4
-    ms = float(np.median(t_grp))
+    # group search: hit x (staged once per event), group offsets, VELO state
+    # and trk_off read, track slots written
+    alg_find = 4 * n + (E * 4 * gg.n_groups + 1) * 4 + 17 * T + 4 * (E + 1) + 34 * T
+    ms, ms_d, ms_f = (float(np.median(v)) for v in (t_grp, t_dec, t_find))
     peak, _ = peaks()
+    found = int(tracks.found[:T].sum().item())
     ctx.close()
     return {"workload": "1000 events, 4 planes x 48 columns x 4 rows of sensors, 84 groups, hits/event 4000, "
                         "tracks/event 200",
-            "hits": n, "decode_bank_order_ms": float(np.median(t_dec)), "sector_groups_ms": ms,
-            "events_per_s": E / (float(np.median(t_dec)) + ms) * 1e3,
-            "algorithmic_bytes": alg, "achieved_gbs": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak}
+            "hits": n, "decode_bank_order_ms": ms_d, "sector_groups_ms": ms,
+            "algorithmic_bytes": alg, "achieved_gbs": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak,
+            "group_search": {"tol_y_mm": tol_y, "ms": ms_f, "found": found, "algorithmic_bytes": alg_find,
+                             "achieved_gbs": alg_find / ms_f / 1e6, "frac": alg_find / ms_f / 1e6 / peak},
+            "events_per_s": E / (ms_d + ms + ms_f) * 1e3,
+            "events_per_s_what": "decode (bank order) + sector groups + group search"}
 
 
 def measure_consolidation(g, ctx, pipe, batch, flush, reps=10):

@@ -63,6 +63,43 @@ typedef struct ut_group_hits {
 int ut_sector_groups(ut_ctx* ctx, const ut_hits* bank_order, int n_events, const ut_group_geometry* gg,
                      ut_group_hits* out, void* stream);
 
+/*
+ * compass_find_groups -- Compass on the sector-group layout: the search of
+ * UT windows over the x regions with two binary searches in y and the
+ * refinement by x (Sec. V-A), then tracklet finding, the p-kick fit and the
+ * selection of compass_find (Sec. V-B).  Per VELO track (state at z_velo,
+ * velo as in compass_find) and layer l:
+ *   u_l  = (x + tx dz) - (y + ty dz) tan_stereo[l], dz = z[l] - z_velo, in
+ *          double; residual of a hit d = (x_hit - (float)u_l) - (float)(u_l -
+ *          (double)(float)u_l) in float;
+ *   the groups searched: c = the number of interior edges k in [1,
+ *          n_groups - 1] with (double)edges[k] <= u_l, then the slot order c,
+ *          c-1, c+1, c-2, c+2 (p->n_sectors of them, inside [0, n_groups));
+ *   y window of a group: y = (float)(y + ty dz) (double inside), ylo = y -
+ *          tol_y, yhi = y + tol_y (float); the group's hits from the first
+ *          with y_end >= ylo to the last with y_begin <= yhi (two binary
+ *          searches; both columns are non-decreasing inside a group, as
+ *          ut_sector_groups writes them);
+ *   candidates: the y-window hits with -hw_l <= d <= hw_l (hw_l as in
+ *          compass_find, or from the kick map), in slot order then storage
+ *          order.
+ * A track is searched when it is not backward, u_0 lies in [x_min, x_min +
+ * n_columns sector_pitch] and some layer has a candidate.  The tracklet
+ * search, fit, chi2 cut, first-n_candidates rule, forward-then-backward
+ * order, selection and Global Event Cut are those of compass_find, over
+ * the candidates in this order.  out (compass_tracks, one slot per VELO
+ * track): hit indices refer to `hits` (the group layout).  The planes' z,
+ * the columns (n_columns, sector_pitch, x_min), n_groups and edges come
+ * from gg; the stereo angles and z_velo from the context; the context's
+ * kick map applies.  One block per event, one warp per track; no waits, no
+ * scratch.  Errors: UT_ERR_ARG for a bad argument (nothing launched):
+ * n_groups outside [1, 128], edges not increasing, tol_y NaN, parameters
+ * as compass_find.
+ */
+int compass_find_groups(ut_ctx* ctx, const ut_group_hits* hits, const ut_group_geometry* gg,
+                        const velo_tracks* velo, int n_events, uint32_t n_tracks, const compass_params* p,
+                        float tol_y, compass_tracks* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_status"
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
            "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate",
-           "ut_sector_groups")
+           "ut_sector_groups", "compass_find_groups")
 
 
 class UtGeometry(ctypes.Structure):
@@ -127,6 +127,7 @@ def lib():
                 "ut_consolidate_workspace_size": ([I], SZ),
                 "ut_consolidate": ([P, P, I, P, P, P, P, SZ, P], I),
                 "ut_sector_groups": ([P, P, I, P, P, P], I),
+                "compass_find_groups": ([P, P, P, P, I, U32, P, ctypes.c_float, P, P], I),
                 "ut_align_chi2": ([P, P, P, P, U32, P, P, P, P, P, P, P, P, SZ, P], I),
                 "ut_align_refit": ([P, P, P, P, U32, P, P, P, P], I),
                 "ut_align_hvp": ([P, P, P, P, U32, P, P, P, P, P, P], I),
@@ -616,3 +617,14 @@ def group_hits_to_numpy(gh: GroupHitBuffers):
     return dict(x=gh.x[:n].cpu().numpy(), z=gh.z[:n].cpu().numpy(), y_begin=gh.y_begin[:n].cpu().numpy(),
                 y_end=gh.y_end[:n].cpu().numpy(), weight=gh.weight[:n].cpu().numpy(),
                 id=gh.id[:n].cpu().numpy().view(np.uint32), group_off=off)
+
+
+def compass_find_groups(ctx, hits: GroupHitBuffers, gg, velo: VeloBuffers, n_events, params, out: TrackBuffers,
+                        tol_y=10.0, stream=None):
+    """Compass on the sector-group layout (compass_find_groups): windows over
+    the groups with y windows, then compass_find's tracklet search; hit
+    indices refer to the group layout."""
+    h, g, v, p, o = hits.struct(), group_geometry_struct(gg), velo.struct(), params_struct(params), out.struct()
+    _check(lib().compass_find_groups(ctx.handle, ctypes.byref(h), ctypes.byref(g), ctypes.byref(v), int(n_events),
+                                     velo.n_tracks, ctypes.byref(p), float(tol_y), ctypes.byref(o), _stream(stream)),
+           "compass_find_groups")
