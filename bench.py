@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the uneven-workload form comparison, serving and alignment measurements")
+    ap.add_argument("--physics", action="store_true",
+                    help="also run the sectors x candidates physics sweep and the kick-map workload")
     return ap.parse_args()
 
 
@@ -197,21 +199,43 @@ def measured_traffic(kernel, workload):
     return rec.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(batch, params, min_seconds=10.0):
-    """The oracle as it stands, OpenMP over events on all host threads."""
+def _time_oracle(batch, params, threads, min_seconds):
+    """Events/s of the oracle (decode + Compass) over repeated passes of
+    `batch` for at least min_seconds; (events/s, passes, seconds)."""
     import oracle
-    threads = oracle.max_threads()
     n = 0
     t0 = time.perf_counter()
     while True:
         oracle.run_batch(batch, params, n_threads=threads)
-        n += batch.n_events
+        n += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
-            break
-    return {"value": n / el, "unit": "events/s", "cores": threads, "kind": "oracle",
-            "sample": f"the full {batch.n_events}-event workload, repeated {n // batch.n_events}x "
-                      f"({el:.1f} s), decode+sort+windows+tracklets+float and double fits"}
+            return n * batch.n_events / el, n, el
+
+
+def cpu_baseline(batch, params, min_seconds=8.0):
+    """The oracle as it stands: OpenMP over events on all host threads on
+    the bench workload (the reported value), plus one thread on a bounded
+    sample of it, the tiny workload in full and the first 2000 events of
+    the uneven 20000-event workload on all threads."""
+    import oracle
+    import synth
+    threads = oracle.max_threads()
+    v, n, el = _time_oracle(batch, params, threads, min_seconds)
+    out = {"value": v, "unit": "events/s", "cores": threads, "kind": "oracle",
+           "sample": f"the full {batch.n_events}-event workload x{n} ({el:.1f} s), decode+sort+windows+"
+                     f"tracklets+float and double fits"}
+    sub = synth.subset(batch, 0, min(batch.n_events, 100))
+    v1, n1, el1 = _time_oracle(sub, params, 1, 3.0)
+    out["single_thread"] = {"value": round(v1, 1), "cores": 1, "sample": f"first {sub.n_events} events x{n1}"}
+    tiny = make_batch("tiny", 0)
+    vt, nt, _ = _time_oracle(tiny, params, threads, 1.0)
+    out["tiny"] = {"value": round(vt, 1), "cores": threads, "sample": f"all {tiny.n_events} events x{nt}"}
+    unev = make_batch("batched", 0, 2000)
+    vu, nu, _ = _time_oracle(unev, params, threads, 3.0)
+    out["uneven"] = {"value": round(vu, 1), "cores": threads,
+                     "sample": f"first 2000 of the 20000 uneven events x{nu}"}
+    return out
 
 
 def run_reference(args):
@@ -278,8 +302,17 @@ def time_forms_on_uneven_workload(g, params, flush, steps=5):
     ms_b = timed(runner.replay)
     blk_p = 800 if cfg.tracks_per_warp == 8 else 256   # compass_find's best block at that width
     ms_p = timed(lambda: pipe.run_plain(stream, cfg.tracks_per_warp, blk_p))
-    ctx.check(stream, "uneven workload")
     E = batch.n_events
+    # decode alone (sorted and bank order) against the measured HBM bandwidth
+    dec = {}
+    hbm, _ = peaks()
+    algo = algorithmic_bytes(batch)["ut_decode"]
+    for name, srt in (("sorted", True), ("bank_order", False)):
+        ms = timed(lambda: g.ut_decode(ctx, pipe.raw, pipe.n_words, pipe.ev_off, E, pipe.hits_a, srt,
+                                       pipe.workspace, stream))
+        gbs = algo / (ms / 1e3) / 1e9
+        dec[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
+    ctx.check(stream, "uneven workload")
     out = {"workload": f"{E} events, hits/event lognormal (median 3000, sigma 0.6, 500-15000), "
                        f"tracks/event 0.05*hits, 4x256 sectors",
            "batched_form": {"ms": round(ms_b, 4), "events_per_s": E / ms_b * 1e3,
@@ -287,18 +320,20 @@ def time_forms_on_uneven_workload(g, params, flush, steps=5):
                                        "graph": True, "kernels_per_step": 1}},
            "plain_form": {"ms": round(ms_p, 4), "events_per_s": E / ms_p * 1e3, "kernels_per_step": 4,
                           "compass_find_block": blk_p},
-           "batched_over_plain": ms_p / ms_b}
+           "batched_over_plain": ms_p / ms_b,
+           "decode_only": dict(dec, algorithmic_bytes=algo)}
     ctx.close()
     return out
 
 
-def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95)):
+def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95), runs_per_level=5):
     """Serving: requests of 64-4096 events (log-uniform, plain-workload
     occupancy) through the continuous-batching engine, 40 GB budget,
     8 stream slots, persistent launch shape `cfg`: sustained peak (all
     submitted at once), then Poisson arrivals at fractions of that peak
-    (96 requests per level, after an untimed open-loop pass); p50/p99
-    request latency."""
+    (runs_per_level runs of 96 requests per level, after an untimed
+    open-loop pass); p50/p99 request latency as the median over the runs,
+    and the largest p99 of the runs."""
     import numpy as np
     import synth
     from paper_2002_11529_gb300 import serve
@@ -317,9 +352,15 @@ def measure_serving(g, params, cfg=None, loads=(0.5, 0.8, 0.95)):
         res["peak_p99_ms"] = peak["p99_ms"]
         serve.run_open_loop(sv, reqs, events_per_s=0.5 * peak["events_per_s"], seed=1)  # warm-up
         for f in loads:
-            summ, _ = serve.run_open_loop(sv, reqs * 4, events_per_s=f * peak["events_per_s"], seed=int(f * 100))
-            res[f"load_{int(round(f * 100))}"] = {k: summ[k] for k in ("events_per_s", "p50_ms", "p99_ms",
-                                                                       "queue_p50_ms", "errors")}
+            runs = [serve.run_open_loop(sv, reqs * 4, events_per_s=f * peak["events_per_s"],
+                                        seed=int(f * 100) + 7 * k)[0] for k in range(runs_per_level)]
+            p50 = [r["p50_ms"] for r in runs]
+            p99 = [r["p99_ms"] for r in runs]
+            res[f"load_{int(round(f * 100))}"] = {
+                "events_per_s": statistics.median(r["events_per_s"] for r in runs),
+                "p50_ms": statistics.median(p50), "p99_ms": statistics.median(p99),
+                "p99_ms_max": max(p99), "p99_ms_runs": [round(v, 3) for v in p99],
+                "errors": sum(len(r["errors"]) for r in runs)}
         res["arena_peak_bytes"] = sv.stats()["arena_peak"]
     return res
 
@@ -584,6 +625,40 @@ def e2e_through_server(g, batch, params, cfg, steps, n_slots=4):
     return wall, h2d, d2h
 
 
+def summarize_variants(d):
+    """The compact summary of the variant measurements kept at the end of
+    the bench line (the full figures are printed on the detail lines)."""
+    r = lambda v, n=4: None if v is None else round(float(v), n)
+    out = {}
+    u = d.get("uneven_workload")
+    if u:
+        out["uneven_20000"] = {"batched_ev_s": r(u["batched_form"]["events_per_s"], 0),
+                               "plain_ev_s": r(u["plain_form"]["events_per_s"], 0),
+                               "batched_over_plain": r(u["batched_over_plain"], 3),
+                               "decode_sorted_frac": u["decode_only"]["sorted"]["frac"],
+                               "decode_bank_order_frac": u["decode_only"]["bank_order"]["frac"]}
+    sv = d.get("serving")
+    if sv:
+        out["serving"] = {"peak_ev_s": r(sv["peak_events_per_s"], 0)}
+        for k in ("load_50", "load_80", "load_95"):
+            if k in sv:
+                out["serving"][k] = {"p50_ms": r(sv[k]["p50_ms"], 3), "p99_ms": r(sv[k]["p99_ms"], 3),
+                                     "p99_ms_max": r(sv[k]["p99_ms_max"], 3)}
+    a = d.get("alignment")
+    if a:
+        out["alignment"] = {"solve_20_ms": r(a["solve_20_steps_ms"], 3),
+                            "chi2_per_track": [r(a["chi2_per_track"][k], 3)
+                                               for k in ("start", "after_20_steps", "truth")]}
+    c = d.get("consolidation")
+    if c:
+        out["consolidation"] = {"ms": r(c["ms"]), "frac": r(c["frac"])}
+    sg = d.get("sector_groups")
+    if sg:
+        out["sector_groups"] = {"layout_frac": r(sg["frac"]), "search_ms": r(sg["group_search"]["ms"]),
+                                "ev_s": r(sg["events_per_s"], 0)}
+    return out
+
+
 def algorithmic_bytes(batch):
     """Minimum bytes each kernel must move for one batch."""
     E, B, H, T = batch.n_events, batch.geom.n_banks, batch.n_hits, batch.n_tracks
@@ -794,16 +869,25 @@ def main():
         "clocks": clk,
         "wall_s": wall,
     }
+    detail = {"autotune": line.pop("autotune")}
     if not args.no_variants and world == 1:
-        line["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
-        line["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
-        line["alignment"] = measure_alignment(g, params)
-        line["physics_sweep"] = physics_sweep(g, batch, params)
-        line["kick_map"] = measure_kick_map(g, params, cfg if args.form == "batched" else g.LaunchConfig(8, 512))
-        line["consolidation"] = measure_consolidation(g, ctx, pipe, batch, flush)
-        line["sector_groups"] = measure_sector_groups(g)
+        detail["uneven_workload"] = time_forms_on_uneven_workload(g, params, flush)
+        detail["serving"] = measure_serving(g, params, cfg if args.form == "batched" else None)
+        detail["alignment"] = measure_alignment(g, params)
+        detail["consolidation"] = measure_consolidation(g, ctx, pipe, batch, flush)
+        detail["sector_groups"] = measure_sector_groups(g)
+        if args.physics:
+            detail["physics_sweep"] = physics_sweep(g, batch, params)
+            detail["kick_map"] = measure_kick_map(g, params,
+                                                  cfg if args.form == "batched" else g.LaunchConfig(8, 512))
+        line["variants"] = summarize_variants(detail)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(batch, params)
+    # full measurements first (lines that are not JSON objects), then the
+    # bench line, whose last keys hold the compact summary
+    for k, v in detail.items():
+        if v is not None:
+            print(f"detail {k} {json.dumps(v)}", flush=True)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

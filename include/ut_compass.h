@@ -153,6 +153,32 @@ int ut_ctx_destroy(ut_ctx* ctx);
  */
 int ut_ctx_set_kick_map(ut_ctx* ctx, int nx, int ny, float tx_max, float ty_max, const float* host_values);
 
+/*
+ * ut_ctx_set_wait_limit -- how long the context's kernels wait for another
+ * block before giving up: the number of polls (each followed by a sleep of
+ * tens of nanoseconds) of a bounded device wait -- the look-back of the
+ * single-pass prefix sums of ut_decode, ut_run_batched and ut_consolidate,
+ * and the bulk copy's barrier.  When it runs out the kernel records
+ * UT_ERR_TIMEOUT (at the waiting event) and carries on with the values it
+ * has, so it always returns; the outputs are then unspecified.  spins <= 0
+ * restores the default, 2^22 polls (about half a second).  Takes effect at
+ * the next launch.  (No counterpart in the paper: the kernels never hang a
+ * shared GPU.)
+ */
+int ut_ctx_set_wait_limit(ut_ctx* ctx, long long spins);
+
+/*
+ * ut_ctx_set_first_ticket -- test facility for the bounded waits: the first
+ * work ticket that ut_decode and ut_run_batched hand out on this context
+ * (default 0).  With first > 0 the events [0, first) are never decoded, so
+ * every later event's look-back waits for a predecessor that never
+ * publishes: each such wait runs out (ut_ctx_set_wait_limit), UT_ERR_TIMEOUT
+ * is recorded at the first waiting event, and the kernel returns; the
+ * outputs are unspecified.  Set it back to 0 for normal use.  UT_ERR_ARG for
+ * first < 0.
+ */
+int ut_ctx_set_first_ticket(ut_ctx* ctx, int first);
+
 /* Synchronise `stream`, then report the recorded device error (0 if none):
  * *code = UT_ERR_*, *where_a = event (-1 if global), *where_b = bank or
  * track index within the event (-1 if global).  Does not clear it. */

@@ -23,7 +23,8 @@ UT_ERR_CAPACITY, UT_ERR_WIN16, UT_ERR_TIMEOUT, UT_ERR_CUDA = -5, -6, -7, -8
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPACITY",
              -6: "WIN16", -7: "TIMEOUT", -8: "CUDA"}
 
-EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_status", "ut_status_reset",
+EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_ctx_set_wait_limit",
+           "ut_ctx_set_first_ticket", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
            "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate",
@@ -114,6 +115,8 @@ def lib():
                 "ut_ctx_create": ([P, P], I),
                 "ut_ctx_destroy": ([P], I),
                 "ut_ctx_set_kick_map": ([P, I, I, ctypes.c_float, ctypes.c_float, P], I),
+                "ut_ctx_set_wait_limit": ([P, ctypes.c_longlong], I),
+                "ut_ctx_set_first_ticket": ([P, I], I),
                 "ut_status": ([P, P, P, P, P], I),
                 "ut_status_reset": ([P, P], I),
                 "ut_decode_workspace_size": ([I], SZ),
@@ -226,6 +229,14 @@ class Context:
         _check(lib().ut_ctx_set_kick_map(self.handle, int(kick_map.nx), int(kick_map.ny),
                                          float(kick_map.tx_max), float(kick_map.ty_max),
                                          v.ctypes.data_as(ctypes.c_void_p)), "ut_ctx_set_kick_map")
+
+    def set_wait_limit(self, spins=0):
+        """Polls of a bounded device wait before UT_ERR_TIMEOUT (0 = default)."""
+        _check(lib().ut_ctx_set_wait_limit(self.handle, int(spins)), "ut_ctx_set_wait_limit")
+
+    def set_first_ticket(self, first=0):
+        """Test facility: the decodes skip events [0, first) (ut_ctx_set_first_ticket)."""
+        _check(lib().ut_ctx_set_first_ticket(self.handle, int(first)), "ut_ctx_set_first_ticket")
 
     def check(self, stream=None, what="device"):
         code, a, b = self.status(stream)

@@ -102,6 +102,9 @@ __device__ __forceinline__ void batched_body(const DecodeArgs& D, const FindArgs
         if (e >= D.n_events) break;
         decode_event<true>(D, e, sm, phase, tma_ok, sx, A.x_cap);
         __syncthreads();
+        // a bulk copy may still land in the stage region, which the search
+        // state overlays: stop (the timeout is recorded; outputs unspecified)
+        if (!tma_ok) break;
         const uint32_t total = sm.off[B];
         const unsigned long long base = s_base;
         if (base + total > (unsigned long long)D.capacity) continue;  // reported by decode_event
@@ -119,7 +122,7 @@ __device__ __forceinline__ void batched_body(const DecodeArgs& D, const FindArgs
             compass_warp<G>(A, heads + gw, ft, Q, X, sm.off, (uint32_t)base, e, t0 + k, k < wb, search, gl, gmask);
         }
     }
-    drain_stage(sm, phase, tma_ok);
+    drain_stage(sm, phase, tma_ok, D.spin_limit);
 }
 
 template <int G, int NT>
@@ -130,6 +133,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ut_batched_kernel(const DecodeAr
 __global__ void __launch_bounds__(kLargeBlockMax, 1) ut_batched_large_kernel(const DecodeArgs D, const FindArgs A) {
     batched_body<4, 0>(D, A);
 }
+
+// First work ticket (ut_ctx_set_first_ticket; tests of the bounded waits).
+__global__ void set_first_ticket_kernel(unsigned int* ticket, unsigned int v) { *ticket = v; }
 
 template <int G, int NT>
 static int launch_batched(const DecodeArgs& D, const FindArgs& A, int block, const ut_ctx* ctx, cudaStream_t st) {
@@ -239,7 +245,12 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.stage_words = (uint32_t)stage_words;
     D.map_cap = 4 * S <= 1024 ? kMapCapDefault : 0;  // sorted bank-map path (bank and rank share 16 bits)
     D.vec_ok = hits_aligned16(hits_out);
+    D.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
+    if (ctx->first_ticket) {
+        set_first_ticket_kernel<<<1, 1, 0, st>>>(D.ticket, ctx->first_ticket);
+        if (cudaGetLastError() != cudaSuccess) return UT_ERR_CUDA;
+    }
     switch (tpw) {
         case 1: return launch_batched_g<32>(D, A, block, ctx, st);
         case 2: return launch_batched_g<16>(D, A, block, ctx, st);

@@ -24,8 +24,9 @@ __device__ __forceinline__ void report(unsigned long long* status, int code, lon
     atomicMin(status, err_key(code, a, b));
 }
 
-// Upper bound on spin iterations of any device-side wait (~0.5 s with the
+// Default upper bound on the polls of a device-side wait (~0.5 s with the
 // back-off below); past it the kernel records UT_ERR_TIMEOUT and moves on.
+// A context can lower it (ut_ctx_set_wait_limit).
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -75,9 +76,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; returns false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
+// Bounded wait on an mbarrier phase; returns false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 64) __nanosleep(64);
     }
@@ -127,6 +128,8 @@ struct ut_ctx {
     float* d_kmap;
     int kmap_nx, kmap_ny;
     float kmap_tx_max, kmap_ty_max, kmap_max;
+    long long wait_limit;   // polls of a bounded device wait (ut_ctx_set_wait_limit)
+    unsigned first_ticket;  // first work ticket of the decodes (ut_ctx_set_first_ticket)
 };
 
 namespace utc {

@@ -22,6 +22,7 @@ struct ConsArgs {
     unsigned int* ticket;
     unsigned long long* tile_state;
     unsigned long long* status;
+    long long spin_limit;
 };
 
 __global__ void __launch_bounds__(kConsThreads) ut_consolidate_kernel(const ConsArgs a) {
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kConsThreads) ut_consolidate_kernel(const Cons
     if (tid < 32) {
         if (tid == 0)
             st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
-        const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
+        const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status, a.spin_limit) : 0ull;
         if (tid == 0) {
             if (e > 0) st_volatile_u64(a.tile_state + e, kFlagPrefix | ((excl + total) & kValueMask));
             s_base = excl;
@@ -128,6 +129,7 @@ extern "C" int ut_consolidate(ut_ctx* ctx, const uint32_t* d_trk_off, int n_even
     a.ticket = static_cast<unsigned int*>(d_workspace);
     a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     a.status = ctx->d_status;
+    a.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_consolidate_workspace_size(n_events), st) != cudaSuccess)
         return UT_ERR_CUDA;
     ut_consolidate_kernel<<<n_events, kConsThreads, 0, st>>>(a);

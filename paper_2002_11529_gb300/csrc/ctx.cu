@@ -16,6 +16,8 @@ extern "C" int ut_ctx_create(ut_ctx** out, const ut_geometry* geom) {
     ut_ctx* c = new (std::nothrow) ut_ctx();
     if (!c) return UT_ERR_ARG;
     c->geom = g;
+    c->wait_limit = kSpinLimit;
+    c->first_ticket = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess ||
@@ -70,6 +72,18 @@ extern "C" int ut_ctx_set_kick_map(ut_ctx* c, int nx, int ny, float tx_max, floa
     c->kmap_tx_max = tx_max;
     c->kmap_ty_max = ty_max;
     c->kmap_max = vmax;
+    return UT_OK;
+}
+
+extern "C" int ut_ctx_set_wait_limit(ut_ctx* c, long long spins) {
+    if (!c) return UT_ERR_ARG;
+    c->wait_limit = spins > 0 ? spins : kSpinLimit;
+    return UT_OK;
+}
+
+extern "C" int ut_ctx_set_first_ticket(ut_ctx* c, int first) {
+    if (!c || first < 0) return UT_ERR_ARG;
+    c->first_ticket = (unsigned)first;
     return UT_OK;
 }
 

@@ -57,8 +57,12 @@ __global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeA
     uint32_t phase = 0;
     bool tma_ok = true;
     decode_event<SORT>(a, e, sm, phase, tma_ok, nullptr, 0);
-    drain_stage(sm, phase, tma_ok);
+    drain_stage(sm, phase, tma_ok, a.spin_limit);
 }
+
+// First work ticket of a decode (ut_ctx_set_first_ticket; tests of the
+// bounded waits).
+__global__ void set_ticket_kernel(unsigned int* ticket, unsigned int v) { *ticket = v; }
 
 // ---------------------------------------------------------------------------
 // ut_sort_hits: stable per-bank sort of decoded hits by half-strip (the
@@ -216,7 +220,12 @@ extern "C" int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_word
     a.stage_words = kStageWordsDefault;
     a.map_cap = B <= 65536 ? kMapCapDefault : 0;
     a.vec_ok = hits_aligned16(out);
+    a.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
+    if (ctx->first_ticket) {
+        set_ticket_kernel<<<1, 1, 0, st>>>(a.ticket, ctx->first_ticket);
+        if (cudaGetLastError() != cudaSuccess) return UT_ERR_CUDA;
+    }
     const size_t smem = decode_smem_bytes(B, sorted != 0, a.stage_words, a.map_cap);
     cudaError_t err;
     if (sorted) {
@@ -335,6 +344,7 @@ extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw,
     a.stage_words = kStageWordsDefault;
     a.map_cap = B <= 65536 ? kMapCapDefault : 0;
     a.vec_ok = hits_aligned16(out);
+    a.spin_limit = kSpinLimit;
     // the array keeps the previous call's contents: clear the counter and the
     // look-back state of the events used here
     if (cudaMemsetAsync(scratch, 0, 16 + (size_t)n_events * sizeof(unsigned long long), st) != cudaSuccess)

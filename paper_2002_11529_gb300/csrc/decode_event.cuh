@@ -49,6 +49,7 @@ struct DecodeArgs {
     uint32_t stage_words;
     uint32_t map_cap;            // events up to this many hits use the mapped, vector-store path
     int vec_ok;                  // output arrays are 16-byte aligned
+    long long spin_limit;        // polls of a bounded wait before UT_ERR_TIMEOUT
 };
 
 // All five output arrays start on a 16-byte boundary (vector stores allowed).
@@ -140,7 +141,8 @@ static __device__ uint32_t block_exclusive_scan(uint32_t* cnt, int n, uint32_t* 
 // each step reads the states of 128 predecessors (four per lane, lane-major
 // by distance) and waits only for those nearer than the nearest inclusive
 // prefix.
-static __device__ unsigned long long lookback(unsigned long long* tile_state, int e, unsigned long long* status) {
+static __device__ unsigned long long lookback(unsigned long long* tile_state, int e, unsigned long long* status,
+                                              long long spin_limit) {
     const int lane = threadIdx.x & 31;
     unsigned long long excl = 0;
     int j = e - 1;  // nearest predecessor not yet summed
@@ -169,7 +171,7 @@ static __device__ unsigned long long lookback(unsigned long long* tile_state, in
                 missing |= needed && (st[t] >> 62) == 0;
             }
             if (!__any_sync(0xffffffffu, missing)) break;
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (lane == 0) report(status, UT_ERR_TIMEOUT, e, -1);
                 return excl;
             }
@@ -415,8 +417,10 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
 
 // Decode event e with the whole block.  `phase` is the parity of the bulk
 // copy barrier's next phase (toggled when a copy completes); `tma_ok` turns
-// false after a copy that did not complete within the wait limit (the
-// caller then waits once more, bounded, before it exits).  sx (nullable)
+// false (for the whole block) after a copy that did not complete within two
+// wait limits: the stage region may still receive it, so the caller stops
+// using shared memory that overlaps the stage (it waits once more, bounded,
+// before it exits).  sx (nullable)
 // receives the event-local decoded x of positions < sx_cap.  On return
 // (after a __syncthreads by the caller) sm.off holds the event-local
 // offsets and *sm.s_base the event's global base.
@@ -450,12 +454,19 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
                     done += chunk;
                 }
             }
-            if (mbar_wait_bounded(sm.mbar, phase)) {
+            // the outcome is made the same for the whole block
+            if (__syncthreads_and(mbar_wait_bounded(sm.mbar, phase, a.spin_limit))) {
                 evw = stage + (ws - al0);
                 phase ^= 1u;
             } else {
+                // the copy did not complete in time: record it, read this
+                // event from global memory, and wait (bounded) once more so
+                // that the copy cannot land later in shared memory the block
+                // reuses; if it is still in flight the block stops using the
+                // stage region (tma_ok = false: the caller ends its work)
                 if (tid == 0) report(a.status, UT_ERR_TIMEOUT, e, -1);
-                tma_ok = false;
+                if (__syncthreads_and(mbar_wait_bounded(sm.mbar, phase, a.spin_limit))) phase ^= 1u;
+                else tma_ok = false;
             }
         }
     } else if (tid == 0) {
@@ -497,7 +508,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     const bool mapped = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
     if (mapped) map_event<SORT>(a, sm, evw, total, any_big);
     if (tid < 32) {
-        const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status) : 0ull;
+        const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status, a.spin_limit) : 0ull;
         if (tid == 0) {
             if (e > 0) st_volatile_u64(a.tile_state + e, kFlagPrefix | ((excl + total) & kValueMask));
             *sm.s_base = excl;
@@ -552,7 +563,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
 namespace utc {
 // Before a block exits after a bulk copy that timed out: wait (bounded) for
 // the copy still in flight so that it does not land in freed shared memory.
-__device__ __forceinline__ void drain_stage(const DecodeSmem& sm, uint32_t phase, bool tma_ok) {
-    if (!tma_ok) (void)mbar_wait_bounded(sm.mbar, phase);
+__device__ __forceinline__ void drain_stage(const DecodeSmem& sm, uint32_t phase, bool tma_ok, long long limit) {
+    if (!tma_ok) (void)mbar_wait_bounded(sm.mbar, phase, limit);
 }
 }  // namespace utc

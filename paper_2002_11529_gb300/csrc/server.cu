@@ -8,9 +8,12 @@
 // thread admits waiting requests in arrival order as soon as a slot is idle
 // and the arena can hold the request's buffers; an admitted request's
 // copies in, its single batched launch (ut_run_batched) and its copies out
-// are enqueued on the slot's stream, so requests overlap on the device.
-// Completion is detected with an event; the request's arena block is then
-// freed and its latency (submission to completion, host clock) recorded.
+// are enqueued on the slot's stream -- outside the engine's lock, so that
+// submissions and polls never wait behind an enqueue -- and requests overlap
+// on the device.  A host function enqueued after the copies out marks the
+// request complete as soon as the stream reaches it (no polling): the
+// request's arena block is freed, its latency (submission to completion,
+// host clock) recorded and the worker woken for the next admissions.
 
 #include <algorithm>
 #include <chrono>
@@ -82,9 +85,9 @@ struct Request {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
     ut_ctx* ctx = nullptr;
     Request* req = nullptr;
+    ut_server* sv = nullptr;
 };
 
 }  // namespace utc
@@ -160,8 +163,9 @@ static void set_error(Request* q, int rc) {
     if (q->status == UT_OK) q->status = rc;
 }
 
-// Enqueue one admitted request on its slot's stream (called with the lock
-// held; only enqueues work).
+// Enqueue one admitted request's copies, launch and copies out on its slot's
+// stream (called without the engine's lock: the slot and the arena block
+// belong to this request until it completes; only enqueues work).
 static void launch_request(ut_server* sv, Slot& sl, Request* q) {
     const ut_server_request& r = q->in;
     const Layout L = layout_of(r, sv->geom.n_sectors);
@@ -226,36 +230,44 @@ static void launch_request(ut_server* sv, Slot& sl, Request* q) {
     if (cudaMemcpyAsync(sl.ctx->h_status, sl.ctx->d_status, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         st) != cudaSuccess)
         set_error(q, UT_ERR_CUDA);
-    if (cudaEventRecord(sl.done, st) != cudaSuccess) set_error(q, UT_ERR_CUDA);
+}
+
+// Completion of a slot's request, with the engine's lock held: the status
+// word (copied to page-locked memory before the host function ran), the
+// arena block freed, the result queued for ut_server_poll.
+static void finish_request(ut_server* sv, Slot& sl) {
+    Request* r = sl.req;
+    r->t_done = Clock::now();
+    const unsigned long long k = *sl.ctx->h_status;
+    if (k != ~0ull && r->status == UT_OK) {
+        r->status = -(int)(k & 0xFF);
+        const unsigned long long a = k >> 32, b = (k >> 8) & 0xFFFFFF;
+        r->where_a = a == 0xFFFFFFFFull ? -1 : (int64_t)a;
+        r->where_b = b == 0xFFFFFFull ? -1 : (int64_t)b;
+    }
+    sv->arena->release(r->off, r->bytes);
+    sl.req = nullptr;
+    sv->finished.push_back(r);
+    --sv->in_flight;
+}
+
+// Host function enqueued after a request's copies out: runs on a CUDA
+// driver thread once the stream has reached it (it makes no CUDA call).
+static void CUDART_CB on_request_done(void* user) {
+    Slot* sl = static_cast<Slot*>(user);
+    ut_server* sv = sl->sv;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    finish_request(sv, *sl);
+    sv->cv.notify_all();
 }
 
 static void worker_loop(ut_server* sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
+    std::vector<Slot*> admitted;
     while (true) {
-        bool progressed = false;
-        // completions
-        for (Slot& sl : sv->slots) {
-            if (!sl.req) continue;
-            const cudaError_t q = cudaEventQuery(sl.done);
-            if (q == cudaErrorNotReady) continue;
-            Request* r = sl.req;
-            r->t_done = Clock::now();
-            if (q != cudaSuccess) set_error(r, UT_ERR_CUDA);
-            const unsigned long long k = *sl.ctx->h_status;
-            if (k != ~0ull && r->status == UT_OK) {
-                r->status = -(int)(k & 0xFF);
-                const unsigned long long a = k >> 32, b = (k >> 8) & 0xFFFFFF;
-                r->where_a = a == 0xFFFFFFFFull ? -1 : (int64_t)a;
-                r->where_b = b == 0xFFFFFFull ? -1 : (int64_t)b;
-            }
-            sv->arena->release(r->off, r->bytes);
-            sl.req = nullptr;
-            sv->finished.push_back(r);
-            --sv->in_flight;
-            progressed = true;
-        }
         // admissions, in arrival order, while a slot and memory are free
+        admitted.clear();
         while (!sv->pending.empty()) {
             Request* r = sv->pending.front();
             Slot* free_slot = nullptr;
@@ -273,20 +285,27 @@ static void worker_loop(ut_server* sv) {
             r->slot = (int)(free_slot - sv->slots.data());
             free_slot->req = r;
             sv->peak_used = std::max(sv->peak_used, sv->arena->used());
-            launch_request(sv, *free_slot, r);
-            progressed = true;
+            admitted.push_back(free_slot);
         }
-        if (progressed) sv->cv.notify_all();
+        if (!admitted.empty()) {
+            // enqueue outside the lock; the slots stay owned by their requests
+            lk.unlock();
+            for (Slot* sl : admitted) {
+                launch_request(sv, *sl, sl->req);
+                if (cudaLaunchHostFunc(sl->stream, on_request_done, sl) != cudaSuccess) {
+                    cudaStreamSynchronize(sl->stream);  // the request can still be finished here
+                    std::lock_guard<std::mutex> g(sv->mu);
+                    set_error(sl->req, UT_ERR_CUDA);
+                    finish_request(sv, *sl);
+                    sv->cv.notify_all();
+                }
+            }
+            lk.lock();
+            continue;
+        }
         if (sv->stop && sv->pending.empty() && sv->in_flight == 0) break;
-        if (!progressed) {
-            // idle: wait for a submission, or poll the streams again shortly
-            bool busy = false;
-            for (Slot& sl : sv->slots) busy |= sl.req != nullptr;
-            if (busy)
-                sv->cv.wait_for(lk, std::chrono::microseconds(20));
-            else
-                sv->cv.wait_for(lk, std::chrono::milliseconds(5));
-        }
+        // wait for a submission or a completion (both notify)
+        sv->cv.wait(lk);
     }
 }
 
@@ -316,8 +335,8 @@ extern "C" int ut_server_create(ut_server** out, const ut_geometry* geom, const 
     sv->arena = new Arena(sv->budget);
     sv->slots.resize(n_slots);
     for (Slot& sl : sv->slots) {
+        sl.sv = sv;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             ut_ctx_create(&sl.ctx, geom) != UT_OK) {
             ut_server_destroy(sv);
             return UT_ERR_CUDA;
@@ -390,7 +409,6 @@ extern "C" int ut_server_destroy(ut_server* sv) {
     for (Slot& sl : sv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.ctx) ut_ctx_destroy(sl.ctx);
-        if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     for (Request* q : sv->finished) delete q;
