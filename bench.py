@@ -369,7 +369,8 @@ def measure_alignment(g, params, reps=10):
     """Alignment on the 100k-track, 4 x 256-sector set (3072 parameters):
     device times of one chi2 + adjoint pass (gradients and Gauss-Newton
     blocks), one refit, one reduced Hessian-vector product, and the 20-step
-    solve (CUDA events, L2 flushed before each timed call)."""
+    solve (ut_align_solve: the whole loop on the device; CUDA events, L2
+    flushed before each timed call)."""
     import numpy as np
     import torch
     import synth
@@ -413,6 +414,7 @@ def measure_alignment(g, params, reps=10):
     est, hist = align.solve_alignment(prob, steps=20)
     e1.record()
     e1.synchronize()
+    hist = hist.tolist()
     c_true = prob.chi2(prob.refit(al), al)[0].item()
     res["solve_20_steps_ms"] = e0.elapsed_time(e1)
     res["chi2_per_track"] = {"start": hist[0] / a.n_tracks, "after_20_steps": hist[-1] / a.n_tracks,

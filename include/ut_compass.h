@@ -42,7 +42,10 @@ enum {
     UT_ERR_CAPACITY = -5, /* more hits than ut_hits.capacity (or 2^32-1)       */
     UT_ERR_WIN16 = -6,    /* a window does not fit the int16 (first, size)     */
     UT_ERR_TIMEOUT = -7,  /* a bounded device-side wait ran out                */
-    UT_ERR_CUDA = -8      /* a CUDA runtime call failed                        */
+    UT_ERR_CUDA = -8,     /* a CUDA runtime call failed                        */
+    UT_ERR_BOUNDS = -9    /* bounds-checked build only: an index outside its
+                             array (where_b = the access site); the access
+                             was skipped                                      */
 };
 
 /* Detector description (Sec. III-A: four planes UTaX, UTaU, UTbV, UTbX, the
@@ -105,10 +108,21 @@ typedef struct compass_params {
     int gec_max_hits;       /* Global Event Cut (Sec. VI): the tracks of an event
                              * with more UT hits are not searched (found = 0,
                              * windows -1); 0 = no cut                        */
+    int output_order;       /* 0: each VELO track's result in its own slot
+                             * (deterministic); 1: the paper's output order
+                             * (Sec. V-B): the found tracks of event e take rows
+                             * trk_off[e] + k, k from an atomic counter of the
+                             * event, so their order inside the event varies
+                             * from run to run (see compass_tracks)          */
 } compass_params;
 
-/* One output slot per VELO track (Sec. V-B output, placed at the track's
- * own index instead of an atomic counter, so results are deterministic). */
+/* Track outputs (Sec. V-B output).  output_order 0 (default): one slot per
+ * VELO track, at the track's own index instead of an atomic counter, so
+ * results are deterministic; velo and n_found are not used (may be NULL).
+ * output_order 1 (the paper's order): row trk_off[e] + k, k < n_found[e],
+ * holds the k-th found track of event e in the order the tracks finished
+ * (an atomic counter per event); velo[row] is its VELO track index; rows
+ * past n_found[e] are not written; the call clears n_found first. */
 typedef struct compass_tracks {
     int32_t* hit;           /* [T][4] global hit index per layer, -1 = none  */
     float* qop;             /* fitted q/p (1/GeV); charge = sign             */
@@ -117,6 +131,8 @@ typedef struct compass_tracks {
     float* tx;              /* fitted tx                                     */
     uint8_t* nhits;         /* 0, 3 or 4                                     */
     uint8_t* found;         /* 1 if a tracklet was selected                  */
+    uint32_t* velo;         /* output_order 1: VELO track index of each row  */
+    uint32_t* n_found;      /* output_order 1: found tracks per event [E]    */
 } compass_tracks;
 
 typedef struct ut_ctx ut_ctx;
@@ -236,7 +252,11 @@ int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_words, const ui
  *     key >> 32, bank = (key >> 8) & 0xFFFFFF (all ones = -1).
  * Nothing is allocated: no cudaMalloc/cudaFree.  The first call on a device
  * looks up the array's device address with that device current (call it
- * once before any stream capture).  Every call on a device shares the one
+ * once before any stream capture) and keeps it for the life of the
+ * device's primary context: a process that calls cudaDeviceReset must not
+ * call ut_decode_noalloc on that device afterwards.  Argument errors
+ * (UT_ERR_ARG) are found before anything is enqueued; d_status is then not
+ * touched.  Every call on a device shares the one
  * array: calls that overlap on the GPU (other streams, other threads) race
  * and must be serialised by the caller.  The call clears the part of the
  * array it uses before the kernel runs.
@@ -278,7 +298,8 @@ int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, int 
  * Sec. V-B) of the hits given in out->hit for n_tracks tracks whose VELO
  * states are velo->x[0..n_tracks) (trk_off unused).  Writes qop, chi2, x,
  * tx; tracks with fewer than 3 hits (or a failed solve) get qop = chi2 = 0,
- * x = VELO x, tx = VELO tx.  nhits and found are not touched.
+ * x = VELO x, tx = VELO tx.  nhits and found are not touched.  Row i is
+ * fitted with VELO state i whatever p->output_order says.
  */
 int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint32_t n_tracks,
                 const compass_params* p, compass_tracks* inout, void* stream);
@@ -398,6 +419,35 @@ int ut_align_hvp(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, cons
                  const double* d_v, double* d_hv, void* stream);
 
 /*
+ * ut_align_solve -- the alignment estimate by preconditioned conjugate
+ * gradients on the reduced Gauss-Newton system of the chi2 above (track
+ * states profiled out by the refit), entirely on the device: no host
+ * synchronisation, every step enqueued on `stream`.  Each linearisation:
+ * ut_align_refit, ut_align_chi2 (gradient and per-sector blocks; its chi2
+ * goes to d_history), the preconditioner = the inverses of the per-sector
+ * 3x3 blocks (cofactors in double; zero for a sector without hits), r = -g,
+ * then up to relinearize_every CG steps, each one ut_align_hvp and the
+ * vector updates (dot products by one block, in a fixed order); then
+ * d_align += the step (float).  `steps` CG steps in all.  A step that meets
+ * p.Hp <= 0 (or not finite) ends the solve after that linearisation's
+ * update; the later kernels of the call then do nothing (their d_history
+ * entries repeat the final chi2).  Finally a refit and the chi2 at the
+ * estimate.
+ *   d_align: [4S][3] float, the start on entry, the estimate on exit;
+ *   d_history: double[ceil(steps / relinearize_every) + 1], the chi2 at the
+ *     start of each linearisation and at the estimate;
+ *   d_workspace: >= ut_align_solve_workspace_size(S, n_tracks) bytes,
+ *     16-byte aligned (refit states, gradient, blocks, solver vectors).
+ * Errors: UT_ERR_ARG for steps < 0, relinearize_every < 1, null or small
+ * buffers (nothing enqueued); those of the calls it makes.  (The "twenty
+ * gradient-descent steps" of the alignment workload read as this solve.)
+ */
+size_t ut_align_solve_workspace_size(int n_sectors, uint32_t n_tracks);
+int ut_align_solve(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* d_track_hits,
+                   uint32_t n_tracks, const compass_params* p, float* d_align, int steps, int relinearize_every,
+                   double* d_history, void* d_workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Serving engine: continuous batching of whole-path requests under a fixed
  * device-memory budget (the paper's multi-stream host framework, Sec. I,
  * as a request loop).  The engine owns one device arena of budget_bytes and
@@ -448,7 +498,8 @@ size_t ut_server_request_bytes(const ut_geometry* geom, const ut_server_request*
 
 /* Create an engine on the current device (allocates the arena, the streams
  * and the worker thread).  cfg: launch shape of the batched kernel (NULL =
- * defaults). */
+ * defaults).  The requests' outputs are per VELO slot: p->output_order must
+ * be 0 (else UT_ERR_ARG). */
 int ut_server_create(ut_server** sv, const ut_geometry* geom, const compass_params* p, size_t budget_bytes,
                      int n_slots, const ut_launch_config* cfg);
 

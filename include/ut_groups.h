@@ -40,7 +40,9 @@ extern "C" {
  * equal to the context's n_sectors; edges strictly increasing.  One block
  * per event, no waits.  Errors: UT_ERR_ARG (host checks, nothing launched);
  * recorded on the device: UT_ERR_CAPACITY if a capacity is below an
- * event's end, UT_ERR_ARG for a hit id naming no sensor of the geometry.
+ * event's end, UT_ERR_ARG for a hit id naming no sensor of the geometry
+ * (such a hit is not placed; the layout of its event is then unspecified,
+ * as every output is when the status reports an error).
  */
 typedef struct ut_group_geometry {
     int n_columns, rows, n_groups;

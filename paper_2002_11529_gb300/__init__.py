@@ -19,15 +19,16 @@ import torch
 from . import build as _build
 
 UT_OK, UT_ERR_ARG, UT_ERR_DIR, UT_ERR_HEADER, UT_ERR_STRIP = 0, -1, -2, -3, -4
-UT_ERR_CAPACITY, UT_ERR_WIN16, UT_ERR_TIMEOUT, UT_ERR_CUDA = -5, -6, -7, -8
+UT_ERR_CAPACITY, UT_ERR_WIN16, UT_ERR_TIMEOUT, UT_ERR_CUDA, UT_ERR_BOUNDS = -5, -6, -7, -8, -9
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "DIR", -3: "HEADER", -4: "STRIP", -5: "CAPACITY",
-             -6: "WIN16", -7: "TIMEOUT", -8: "CUDA"}
+             -6: "WIN16", -7: "TIMEOUT", -8: "CUDA", -9: "BOUNDS"}
 
 EXPORTS = ("ut_ctx_create", "ut_ctx_destroy", "ut_ctx_set_kick_map", "ut_ctx_set_wait_limit",
            "ut_ctx_set_first_ticket", "ut_status", "ut_status_reset",
            "ut_decode_workspace_size", "ut_decode", "ut_sort_hits", "compass_find", "compass_fit",
            "ut_decode_noalloc", "ut_run_batched", "ut_align_workspace_size", "ut_align_chi2",
-           "ut_align_refit", "ut_align_hvp", "ut_consolidate_workspace_size", "ut_consolidate",
+           "ut_align_refit", "ut_align_hvp", "ut_align_solve_workspace_size", "ut_align_solve",
+           "ut_consolidate_workspace_size", "ut_consolidate",
            "ut_sector_groups", "compass_find_groups")
 
 
@@ -64,11 +65,13 @@ class CompassParamsC(ctypes.Structure):
     _fields_ = [("n_sectors", ctypes.c_int), ("n_candidates", ctypes.c_int)] + [
         (n, ctypes.c_float) for n in ("qop_max", "tol_win", "tol_kink", "tol_col", "tol_slope",
                                       "chi2ndof_max", "sigma_hit", "sigma_x_prior",
-                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int)]
+                                      "sigma_tx_prior", "z_kink", "kick_k")] + [("gec_max_hits", ctypes.c_int),
+                                                                                ("output_order", ctypes.c_int)]
 
 
 class CompassTracksC(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found", "velo",
+                                               "n_found")]
 
 
 class UtTracksCompactC(ctypes.Structure):
@@ -98,7 +101,7 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path()
 
 
 def lib():
@@ -106,7 +109,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = _build.lib_path()
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library not built ({path}); run paper_2002_11529_gb300.build.build()")
             L = ctypes.CDLL(path)
@@ -134,6 +137,8 @@ def lib():
                 "ut_align_chi2": ([P, P, P, P, U32, P, P, P, P, P, P, P, P, SZ, P], I),
                 "ut_align_refit": ([P, P, P, P, U32, P, P, P, P], I),
                 "ut_align_hvp": ([P, P, P, P, U32, P, P, P, P, P, P], I),
+                "ut_align_solve_workspace_size": ([I, U32], SZ),
+                "ut_align_solve": ([P, P, P, P, U32, P, P, I, I, P, P, SZ, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -296,6 +301,9 @@ class VeloBuffers:
 
 @dataclasses.dataclass
 class TrackBuffers:
+    """Track outputs (compass_tracks).  velo and n_found (int32 [rows] and
+    [n_events]) are only used by the paper's atomic output order
+    (compass_params.output_order = 1)."""
     hit: torch.Tensor
     qop: torch.Tensor
     chi2: torch.Tensor
@@ -303,19 +311,26 @@ class TrackBuffers:
     tx: torch.Tensor
     nhits: torch.Tensor
     found: torch.Tensor
+    velo: torch.Tensor | None = None
+    n_found: torch.Tensor | None = None
 
     @staticmethod
-    def allocate(n_tracks, device="cuda"):
+    def allocate(n_tracks, device="cuda", n_events=None):
         T = max(int(n_tracks), 1)
         f = lambda: torch.empty(T, dtype=torch.float32, device=device)
-        return TrackBuffers(torch.empty((T, 4), dtype=torch.int32, device=device), f(), f(), f(), f(),
-                            torch.empty(T, dtype=torch.uint8, device=device),
-                            torch.empty(T, dtype=torch.uint8, device=device))
+        tb = TrackBuffers(torch.empty((T, 4), dtype=torch.int32, device=device), f(), f(), f(), f(),
+                          torch.empty(T, dtype=torch.uint8, device=device),
+                          torch.empty(T, dtype=torch.uint8, device=device))
+        if n_events is not None:
+            tb.velo = torch.empty(T, dtype=torch.int32, device=device)
+            tb.n_found = torch.empty(max(int(n_events), 1), dtype=torch.int32, device=device)
+        return tb
 
     def struct(self) -> CompassTracksC:
         c = CompassTracksC()
-        for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found"):
-            setattr(c, n, getattr(self, n).data_ptr())
+        for n in ("hit", "qop", "chi2", "x", "tx", "nhits", "found", "velo", "n_found"):
+            t = getattr(self, n)
+            setattr(c, n, t.data_ptr() if t is not None else None)
         return c
 
 

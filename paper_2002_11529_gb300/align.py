@@ -7,8 +7,9 @@ whose backward is the library's hand-written adjoint (ut_align_chi2).
 
 solve_alignment estimates the alignment by preconditioned conjugate
 gradients on the reduced Gauss-Newton system (track states profiled out by
-a refit): every step is one reduced Hessian-vector product (ut_align_hvp),
-the preconditioner the per-sector 3x3 Gauss-Newton blocks.  The detector
+a refit): every step is one reduced Hessian-vector product, the
+preconditioner the per-sector 3x3 Gauss-Newton blocks; the whole loop runs
+in the library (ut_align_solve), this module only marshals.  The detector
 alone cannot fix three global modes (a layer-wise x shift proportional to
 z - z_kink, absorbed by every track's q/p, and two z scalings about the kink
 plane); starting from zero, the solver leaves them essentially untouched.
@@ -90,63 +91,23 @@ class Chi2Alignment(torch.autograd.Function):
                 g * ga if ctx.needs_input_grad[1] else None, None)
 
 
-def _block_inverse(h6: torch.Tensor) -> torch.Tensor:
-    """Inverse of the per-sector symmetric 3x3 blocks [a b c; b d e; c e f]
-    (h6 = a, b, c, d, e, f) by cofactors in double; zero for sectors without
-    hits (a == 0) or a singular block.  Returns [4S, 3, 3]."""
-    h = h6.to(torch.float64)
-    a, b, c, d, e, f = (h[:, i] for i in range(6))
-    A = d * f - e * e
-    Bc = c * e - b * f
-    C = b * e - c * d
-    D = a * f - c * c
-    E = b * c - a * e
-    F = a * d - b * b
-    det = a * A + b * Bc + c * C
-    ok = (a > 0) & (det != 0)
-    r = torch.where(ok, 1.0 / torch.where(ok, det, torch.ones_like(det)), torch.zeros_like(det))
-    inv = torch.stack([torch.stack([A, Bc, C], -1), torch.stack([Bc, D, E], -1), torch.stack([C, E, F], -1)], -2)
-    return inv * r[:, None, None]
-
-
 def solve_alignment(problem: AlignmentProblem, steps: int = 20, relinearize_every: int = 10,
-                    align0: torch.Tensor | None = None):
+                    align0: torch.Tensor | None = None, stream=None):
     """Estimate the alignment in `steps` preconditioned CG steps (one reduced
-    Hessian-vector product each), re-linearising (refit + new gradient)
-    every `relinearize_every` steps.  Returns (align, history)."""
+    Hessian-vector product each), re-linearising (refit, new gradient and
+    blocks) every `relinearize_every` steps: one ut_align_solve call, the
+    whole loop on the device.  Returns (align, history): the estimate [4S,3]
+    and a device tensor of the chi2 at the start of each linearisation and
+    at the estimate."""
     dev = problem.track_hits.device
-    a = torch.zeros((4 * problem.S, 3), dtype=torch.float32, device=dev) if align0 is None else align0.clone()
-    history = []
-    done = 0
-    while done < steps:
-        theta = problem.refit(a)
-        c2, _, g, hblk = problem.chi2(theta, a, grads=True)
-        history.append(float(c2.item()))
-        Minv = _block_inverse(hblk)
-        apply_m = lambda r: torch.einsum("sij,sj->si", Minv, r)
-        x = torch.zeros((4 * problem.S, 3), dtype=torch.float64, device=dev)
-        r = -g.to(torch.float64)
-        z = apply_m(r)
-        p = z.clone()
-        rz = (r * z).sum()
-        for _ in range(min(relinearize_every, steps - done)):
-            Ap = problem.hvp(theta, a, p)
-            pAp = (p * Ap).sum()
-            if not torch.isfinite(pAp) or pAp <= 0:
-                break
-            alpha = rz / pAp
-            x += alpha * p
-            r -= alpha * Ap
-            z = apply_m(r)
-            rz_new = (r * z).sum()
-            p = z + (rz_new / rz) * p
-            rz = rz_new
-            done += 1
-        else:
-            a = a + x.to(torch.float32)
-            continue
-        a = a + x.to(torch.float32)
-        break
-    theta = problem.refit(a)
-    history.append(float(problem.chi2(theta, a)[0].item()))
+    a = torch.zeros((4 * problem.S, 3), dtype=torch.float32, device=dev) if align0 is None else \
+        align0.to(torch.float32).contiguous().clone()
+    n_hist = (steps + relinearize_every - 1) // relinearize_every + 1
+    history = torch.empty(n_hist, dtype=torch.float64, device=dev)
+    nws = int(lib().ut_align_solve_workspace_size(problem.S, problem.n_tracks))
+    ws = torch.empty((nws + 15) // 16 * 2, dtype=torch.float64, device=dev)
+    _check(lib().ut_align_solve(problem.ctx.handle, ctypes.byref(problem._h), ctypes.byref(problem._v),
+                                _ptr(problem.track_hits), problem.n_tracks, ctypes.byref(problem._p), _ptr(a),
+                                int(steps), int(relinearize_every), _ptr(history), _ptr(ws), ws.numel() * 8,
+                                _stream(stream)), "ut_align_solve")
     return a, history

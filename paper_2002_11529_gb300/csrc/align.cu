@@ -48,6 +48,8 @@ struct AlignArgs {
     int want_grad, want_hess;
     const double* v;             // HVP direction [4S][3]
     double* hv;                  // HVP output [4S][3]
+    uint32_t hcap;               // entries of the hit arrays
+    unsigned long long* status;  // status word (bounds-checked builds)
 };
 
 __device__ __forceinline__ void fix_add(long long* p, double v, double scale) {
@@ -69,8 +71,10 @@ __device__ __forceinline__ bool hit_term(const AlignArgs& A, uint32_t t, int l, 
                                          HitTerm& o) {
     const int32_t h = A.thit[(size_t)t * 4 + l];
     if (h < 0) return false;
+    if (!chk((uint32_t)h < A.hcap, A.status, 601)) return false;
     const int lay = A.hlay[h];
     o.g = lay * A.S + (int)A.hsec[h];
+    if (!chk(lay < 4 && o.g < 4 * A.S, A.status, 602)) return false;
     const double dx = A.align[3 * o.g], dz = A.align[3 * o.g + 1], gam = A.align[3 * o.g + 2];
     const double z = A.z[lay] + dz;
     const double y = (double)A.vy[t] + (double)A.vty[t] * (z - A.z_velo);
@@ -239,6 +243,130 @@ __global__ void __launch_bounds__(256) align_hvp_kernel(const AlignArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Preconditioned conjugate gradients on the reduced Gauss-Newton system, on
+// the device (one block each: the 4S x 3 parameters and their dot products).
+// State in the solver's workspace: Minv [4S][9] (inverse per-sector blocks),
+// x, r, z, p, Ap [4S][3], and scal = {rz, stop, dead}: stop = a step met
+// p.Ap <= 0 (or not finite) in this linearisation; dead = the solve has
+// ended (every later kernel of the solve does nothing).
+// ---------------------------------------------------------------------------
+constexpr int kPcgThreads = 1024;
+
+struct PcgState {
+    double* minv;
+    double* x;
+    double* r;
+    double* z;
+    double* p;
+    double* ap;
+    double* scal;
+    int n4;                      // 4S sectors
+};
+
+// Sum of v over the block (every thread gets it); deterministic order.
+__device__ double pcg_block_sum(double v, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+// z_s = Minv_s r_s for sector s
+__device__ __forceinline__ void pcg_apply_m(const PcgState& P, int s, const double* r3, double* z3) {
+    const double* m = P.minv + 9 * s;
+    for (int i = 0; i < 3; ++i) z3[i] = m[3 * i] * r3[0] + m[3 * i + 1] * r3[1] + m[3 * i + 2] * r3[2];
+}
+
+// Start of a linearisation: Minv from the Gauss-Newton blocks (cofactors in
+// double; zero for a sector without hits or a singular block), r = -g,
+// z = Minv r, p = z, x = 0, rz = r.z.
+__global__ void __launch_bounds__(kPcgThreads) pcg_init_kernel(PcgState P, const float* grad, const float* hess) {
+    __shared__ double red[kPcgThreads / 32];
+    if (P.scal[2] != 0.0) return;
+    double rz = 0.0;
+    for (int s = threadIdx.x; s < P.n4; s += blockDim.x) {
+        const float* h = hess + 6 * s;
+        const double a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5];
+        const double A = d * f - e * e, Bc = c * e - b * f, C = b * e - c * d;
+        const double D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
+        const double det = a * A + b * Bc + c * C;
+        const double ri = (a > 0.0 && det != 0.0) ? 1.0 / det : 0.0;
+        double* m = P.minv + 9 * s;
+        m[0] = A * ri; m[1] = Bc * ri; m[2] = C * ri;
+        m[3] = Bc * ri; m[4] = D * ri; m[5] = E * ri;
+        m[6] = C * ri; m[7] = E * ri; m[8] = F * ri;
+        double r3[3], z3[3];
+        for (int i = 0; i < 3; ++i) r3[i] = -(double)grad[3 * s + i];
+        pcg_apply_m(P, s, r3, z3);
+        for (int i = 0; i < 3; ++i) {
+            P.x[3 * s + i] = 0.0;
+            P.r[3 * s + i] = r3[i];
+            P.z[3 * s + i] = z3[i];
+            P.p[3 * s + i] = z3[i];
+            rz += r3[i] * z3[i];
+        }
+    }
+    rz = pcg_block_sum(rz, red);
+    if (threadIdx.x == 0) {
+        P.scal[0] = rz;
+        P.scal[1] = 0.0;
+    }
+}
+
+// One CG step with Ap = H p (from the HVP kernel): alpha = rz / p.Ap,
+// x += alpha p, r -= alpha Ap, z = Minv r, p = z + (rz' / rz) p.
+__global__ void __launch_bounds__(kPcgThreads) pcg_step_kernel(PcgState P) {
+    __shared__ double red[kPcgThreads / 32];
+    if (P.scal[2] != 0.0 || P.scal[1] != 0.0) return;
+    double pap = 0.0;
+    for (int k = threadIdx.x; k < 3 * P.n4; k += blockDim.x) pap += P.p[k] * P.ap[k];
+    pap = pcg_block_sum(pap, red);
+    if (!isfinite(pap) || pap <= 0.0) {
+        if (threadIdx.x == 0) P.scal[1] = 1.0;
+        return;
+    }
+    const double alpha = P.scal[0] / pap;
+    double rz = 0.0;
+    for (int s = threadIdx.x; s < P.n4; s += blockDim.x) {
+        double r3[3], z3[3];
+        for (int i = 0; i < 3; ++i) {
+            P.x[3 * s + i] += alpha * P.p[3 * s + i];
+            r3[i] = P.r[3 * s + i] - alpha * P.ap[3 * s + i];
+            P.r[3 * s + i] = r3[i];
+        }
+        pcg_apply_m(P, s, r3, z3);
+        for (int i = 0; i < 3; ++i) {
+            P.z[3 * s + i] = z3[i];
+            rz += r3[i] * z3[i];
+        }
+    }
+    rz = pcg_block_sum(rz, red);
+    const double beta = rz / P.scal[0];
+    for (int k = threadIdx.x; k < 3 * P.n4; k += blockDim.x) P.p[k] = P.z[k] + beta * P.p[k];
+    __syncthreads();
+    if (threadIdx.x == 0) P.scal[0] = rz;
+}
+
+// End of a linearisation: align += x (float); after a stopped step the
+// solve ends here.
+__global__ void __launch_bounds__(kPcgThreads) pcg_apply_kernel(PcgState P, float* align) {
+    if (P.scal[2] != 0.0) return;
+    for (int k = threadIdx.x; k < 3 * P.n4; k += blockDim.x) align[k] = align[k] + (float)P.x[k];
+    __syncthreads();
+    if (threadIdx.x == 0 && P.scal[1] != 0.0) P.scal[2] = 1.0;
+}
+
+__global__ void pcg_reset_kernel(double* scal) {
+    scal[0] = 0.0;
+    scal[1] = 0.0;
+    scal[2] = 0.0;
+}
+
 static int make_align_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* thit,
                            uint32_t n_tracks, const compass_params* p, const float* align, AlignArgs& A) {
     if (!ctx || !hits || !velo || !thit || !p || !align) return UT_ERR_ARG;
@@ -275,6 +403,8 @@ static int make_align_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tr
     A.want_grad = A.want_hess = 0;
     A.v = nullptr;
     A.hv = nullptr;
+    A.hcap = hits->capacity;
+    A.status = ctx->d_status;
     return UT_OK;
 }
 
@@ -336,5 +466,94 @@ extern "C" int ut_align_hvp(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
     A.hv = d_hv;
     if (cudaMemsetAsync(d_hv, 0, sizeof(double) * 3 * 4 * ctx->geom.n_sectors, st) != cudaSuccess) return UT_ERR_CUDA;
     if (n_tracks > 0) align_hvp_kernel<<<(n_tracks + 255) / 256, 256, 0, st>>>(A);
+    return check_cuda(cudaGetLastError());
+}
+
+// Workspace of ut_align_solve: the chi2 accumulators, the refit states, the
+// gradient and blocks, then the solver state (16-byte aligned parts).
+struct SolveLayout {
+    size_t acc, theta, grad, hess, minv, x, r, z, p, ap, scal, total;
+};
+
+static SolveLayout solve_layout(int S, uint32_t T) {
+    SolveLayout L;
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        const size_t at = o;
+        o += (n + 15) & ~(size_t)15;
+        return at;
+    };
+    const size_t n4 = (size_t)4 * S;
+    L.acc = take(ut_align_workspace_size(S));
+    L.theta = take(sizeof(float) * 3 * (size_t)T);
+    L.grad = take(sizeof(float) * 3 * n4);
+    L.hess = take(sizeof(float) * 6 * n4);
+    L.minv = take(sizeof(double) * 9 * n4);
+    L.x = take(sizeof(double) * 3 * n4);
+    L.r = take(sizeof(double) * 3 * n4);
+    L.z = take(sizeof(double) * 3 * n4);
+    L.p = take(sizeof(double) * 3 * n4);
+    L.ap = take(sizeof(double) * 3 * n4);
+    L.scal = take(sizeof(double) * 4);
+    L.total = o;
+    return L;
+}
+
+extern "C" size_t ut_align_solve_workspace_size(int n_sectors, uint32_t n_tracks) {
+    if (n_sectors < 1) n_sectors = 1;
+    return solve_layout(n_sectors, n_tracks).total;
+}
+
+extern "C" int ut_align_solve(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, const int32_t* d_track_hits,
+                              uint32_t n_tracks, const compass_params* p, float* d_align, int steps,
+                              int relinearize_every, double* d_history, void* d_workspace, size_t workspace_bytes,
+                              void* stream) {
+    AlignArgs A;
+    int rc = make_align_args(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, A);
+    if (rc != UT_OK) return rc;
+    if (steps < 0 || relinearize_every < 1 || !d_history || !d_workspace || ((uintptr_t)d_workspace & 15u)) return UT_ERR_ARG;
+    const int S = ctx->geom.n_sectors, S4 = 4 * S;
+    const SolveLayout L = solve_layout(S, n_tracks);
+    if (workspace_bytes < L.total) return UT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_workspace);
+    float* theta = reinterpret_cast<float*>(ws + L.theta);
+    float* grad = reinterpret_cast<float*>(ws + L.grad);
+    float* hess = reinterpret_cast<float*>(ws + L.hess);
+    PcgState P;
+    P.minv = reinterpret_cast<double*>(ws + L.minv);
+    P.x = reinterpret_cast<double*>(ws + L.x);
+    P.r = reinterpret_cast<double*>(ws + L.r);
+    P.z = reinterpret_cast<double*>(ws + L.z);
+    P.p = reinterpret_cast<double*>(ws + L.p);
+    P.ap = reinterpret_cast<double*>(ws + L.ap);
+    P.scal = reinterpret_cast<double*>(ws + L.scal);
+    P.n4 = S4;
+    pcg_reset_kernel<<<1, 1, 0, st>>>(P.scal);
+    int done = 0, h = 0;
+    // each linearisation: refit, chi2 with the gradient and blocks (history),
+    // then up to relinearize_every CG steps (one reduced HVP each)
+    while (done < steps) {
+        rc = ut_align_refit(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, theta, stream);
+        if (rc == UT_OK)
+            rc = ut_align_chi2(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, theta, d_history + h, nullptr, grad,
+                               hess, ws + L.acc, ut_align_workspace_size(S), stream);
+        if (rc != UT_OK) return rc;
+        ++h;
+        pcg_init_kernel<<<1, kPcgThreads, 0, st>>>(P, grad, hess);
+        const int n = steps - done < relinearize_every ? steps - done : relinearize_every;
+        for (int k = 0; k < n; ++k) {
+            rc = ut_align_hvp(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, theta, P.p, P.ap, stream);
+            if (rc != UT_OK) return rc;
+            pcg_step_kernel<<<1, kPcgThreads, 0, st>>>(P);
+        }
+        pcg_apply_kernel<<<1, kPcgThreads, 0, st>>>(P, d_align);
+        done += n;
+    }
+    rc = ut_align_refit(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, theta, stream);
+    if (rc == UT_OK)
+        rc = ut_align_chi2(ctx, hits, velo, d_track_hits, n_tracks, p, d_align, theta, d_history + h, nullptr, nullptr,
+                           nullptr, ws + L.acc, ut_align_workspace_size(S), stream);
+    if (rc != UT_OK) return rc;
     return check_cuda(cudaGetLastError());
 }

@@ -247,6 +247,9 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.vec_ok = hits_aligned16(hits_out);
     D.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
+    if (A.atomic_out &&
+        cudaMemsetAsync(tracks_out->n_found, 0, sizeof(uint32_t) * (size_t)n_events, st) != cudaSuccess)
+        return UT_ERR_CUDA;
     if (ctx->first_ticket) {
         set_first_ticket_kernel<<<1, 1, 0, st>>>(D.ticket, ctx->first_ticket);
         if (cudaGetLastError() != cudaSuccess) return UT_ERR_CUDA;

@@ -24,6 +24,51 @@ __device__ __forceinline__ void report(unsigned long long* status, int code, lon
     atomicMin(status, err_key(code, a, b));
 }
 
+// ---------------------------------------------------------------------------
+// Bounds-checked accesses.  In a build with -DUT_CHECKED every access made
+// through these helpers compares its index with the array's extent first; a
+// violation records UT_ERR_BOUNDS at (-1, site) in the status word and the
+// access is skipped (a load yields zero) -- no trap, no fault.  Sites are
+// numbered per file (decode 1xx, Compass 2xx, group search 3xx, persistent
+// kernel 4xx, consolidation 5xx, alignment 6xx).  Without UT_CHECKED the
+// helpers are the plain access and the extents are never computed.
+// ---------------------------------------------------------------------------
+#ifdef UT_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool chk(bool ok, unsigned long long* status, int site) {
+    if constexpr (kChecked) {
+        if (!ok) report(status, UT_ERR_BOUNDS, -1, site);
+        return ok;
+    }
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_chk(const T* p, long long i, long long n, unsigned long long* status, int site) {
+    if constexpr (kChecked) {
+        if (i < 0 || i >= n) {
+            report(status, UT_ERR_BOUNDS, -1, site);
+            return T();
+        }
+    }
+    return p[i];
+}
+
+template <class T>
+__device__ __forceinline__ void st_chk(T* p, long long i, long long n, T v, unsigned long long* status, int site) {
+    if constexpr (kChecked) {
+        if (i < 0 || i >= n) {
+            report(status, UT_ERR_BOUNDS, -1, site);
+            return;
+        }
+    }
+    p[i] = v;
+}
+
 // Default upper bound on the polls of a device-side wait (~0.5 s with the
 // back-off below); past it the kernel records UT_ERR_TIMEOUT and moves on.
 // A context can lower it (ut_ctx_set_wait_limit).

@@ -112,6 +112,8 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
     if (!ctx || !hits || !velo || !p || !out) return UT_ERR_ARG;
     if (p->n_sectors < 1 || p->n_sectors > kMaxSectors || p->n_candidates < 1 || p->gec_max_hits < 0)
         return UT_ERR_ARG;
+    if (p->output_order != 0 && p->output_order != 1) return UT_ERR_ARG;
+    if (p->output_order == 1 && (!out->velo || !out->n_found)) return UT_ERR_ARG;
     if (!(p->sigma_hit > 0.f) || !(p->sigma_x_prior > 0.f) || !(p->sigma_tx_prior > 0.f)) return UT_ERR_ARG;
     const ut_geometry& g = ctx->geom;
     A.hx = hits->x;
@@ -166,6 +168,9 @@ int make_find_args(const ut_ctx* ctx, const ut_hits* hits, const velo_tracks* ve
     A.found = out->found;
     A.win = win;
     A.status = ctx->d_status;
+    A.atomic_out = p->output_order;
+    A.velo_row = out->velo;
+    A.n_found = out->n_found;
     for (int dir = 0; dir < 2; ++dir) {
         const int la = dir ? 3 : 0, lb = dir ? 1 : 2;
         const float r = (p->z_kink - g.z[la]) / (g.z[lb] - g.z[la]);
@@ -283,12 +288,15 @@ extern "C" int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
     FindArgs A;
     const int rc = make_find_args(ctx, hits, velo, n_events, n_tracks, p, out, d_win, A);
     if (rc != UT_OK) return rc;
-    if (n_tracks == 0 || n_events == 0) return UT_OK;
+    if (n_events == 0) return UT_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (A.atomic_out && cudaMemsetAsync(out->n_found, 0, sizeof(uint32_t) * (size_t)n_events, st) != cudaSuccess)
+        return UT_ERR_CUDA;
+    if (n_tracks == 0) return UT_OK;
     if (tracks_per_warp == 0) tracks_per_warp = 1;
     if (block == 0) block = 256;
     if (block < 64 || block % 32 != 0) return UT_ERR_ARG;
     if (block > 256 && (tracks_per_warp != 8 || block > kFindLargeMax)) return UT_ERR_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (tracks_per_warp) {
         case 1: return launch_find<32>(A, block, ctx->num_sms, st);
         case 2: return launch_find<16>(A, block, ctx->num_sms, st);
@@ -300,8 +308,11 @@ extern "C" int compass_find(ut_ctx* ctx, const ut_hits* hits, const velo_tracks*
 
 extern "C" int compass_fit(ut_ctx* ctx, const ut_hits* hits, const velo_tracks* velo, uint32_t n_tracks,
                            const compass_params* p, compass_tracks* inout, void* stream) {
+    if (!p) return UT_ERR_ARG;
+    compass_params ps = *p;
+    ps.output_order = 0;  // rows are fitted with their own VELO states
     FindArgs A;
-    const int rc = make_find_args(ctx, hits, velo, 0, n_tracks, p, inout, nullptr, A);
+    const int rc = make_find_args(ctx, hits, velo, 0, n_tracks, &ps, inout, nullptr, A);
     if (rc != UT_OK) return rc;
     if (n_tracks == 0) return UT_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -83,7 +83,21 @@ struct FindArgs {
     float kmap_tx_max, kmap_ty_max, kmap_sx, kmap_sy;
     float kick_k, qop_max, tol_win, tol_slope;
     float adz[4];                // |z_l - z_kink|
+    // output order (compass_params.output_order): 0 = the VELO track's slot;
+    // 1 = the paper's atomic index per event (velo_row[row] = VELO track)
+    int atomic_out;
+    uint32_t* velo_row;
+    uint32_t* n_found;
 };
+
+// Output row of a found track t of event e: its own slot, or (the paper's
+// order) the next row of its event from the event's atomic counter.
+__device__ __forceinline__ uint32_t output_row(const FindArgs& A, int e, uint32_t t) {
+    if (!A.atomic_out) return t;
+    const uint32_t row = A.trk_off[e] + atomicAdd(A.n_found + e, 1u);
+    A.velo_row[row] = t;
+    return row;
+}
 
 // The kick of a track of direction (tx, ty) from the map: bilinear
 // interpolation, coordinates clamped to the grid, float operations in the
@@ -206,6 +220,7 @@ struct GroupHead {
     int sec0[4];                 // first searched sector
     int cen[4];                  // central sector
     float scale[4];              // union positions per mm (start of lower-bound walks)
+    float hwt[4];                // the track's window half-width per layer (kick map)
     float hi[4], lo[4];          // prediction per layer (float pair)
     int act;                     // track takes part in the current warp search
     int count;                   // valid tracklets found by the warp search
@@ -232,8 +247,17 @@ struct View {
     const uint32_t* off;         // event-local bank offsets (B + 1)
     int S;
     float hi[4], lo[4];
+    unsigned long long* st;      // status word (bounds-checked builds)
 
-    __device__ __forceinline__ float d(int l, int p) const { return (X[p] - hi[l]) - lo[l]; }
+    // X holds the event's off[4 S] hits (the extent is read only when checked)
+    __device__ __forceinline__ float d(int l, int p) const {
+        return (ld_chk(X, p, kChecked ? (long long)off[4 * S] : 0ll, st, 201) - hi[l]) - lo[l];
+    }
+
+    // half-width that maps the union window onto [0, w1 - w0] in lower():
+    // the constant kick's, else the track's own (with a kick map, A.hw[]
+    // holds the map's largest value, which would shift the hint)
+    __device__ __forceinline__ float hw_hint(const FindArgs& A, int l) const { return A.kmap ? h->hwt[l] : A.hw[l]; }
 
     // first union position of layer l with d >= v: start at the
     // interpolated position, then walk (exact, d is non-decreasing)
@@ -275,7 +299,7 @@ __device__ __forceinline__ int collect(const FindArgs& A, const View& V, int l, 
     const int w1 = V.h->wunion[l][1];
     int bi = -1, bc = -1;
     float bd = 0.f;
-    for (int p = V.lower(l, lo, A.hw[l]); p < w1; ++p) {
+    for (int p = V.lower(l, lo, V.hw_hint(A, l)); p < w1; ++p) {
         const float dv = V.d(l, p);
         if (dv > hi) break;
         const float dist = fabsf(dv - pred);
@@ -428,7 +452,7 @@ __device__ __forceinline__ int fast_dir(const FindArgs& A, const View& V, int gl
             const float da = V.d(la, pa);
             float blo, bhi;
             kink_band<DIR>(A, da, blo, bhi);
-            for (int pb = V.lower(lb, blo, A.hw[lb]); pb < wb1; ++pb) {
+            for (int pb = V.lower(lb, blo, V.hw_hint(A, lb)); pb < wb1; ++pb) {
                 const float db = V.d(lb, pb);
                 if (db > bhi) break;
                 Tracklet tk;
@@ -494,7 +518,7 @@ __device__ __forceinline__ int scan_anchor(const FindArgs& A, const View& V, int
     float blo, bhi;
     kink_band<DIR>(A, da, blo, bhi);
     const int wb1 = V.h->wunion[lb][1];
-    const int p0 = V.lower(lb, blo, A.hw[lb]);
+    const int p0 = V.lower(lb, blo, V.hw_hint(A, lb));
     int p1 = p0;
     while (p1 < wb1 && V.d(lb, p1) <= bhi) ++p1;
     int nvalid = 0;
@@ -599,7 +623,7 @@ __device__ __noinline__ void eval_pair_cold(const FindArgs& A, const View& V, in
 // Event Cut): no hits, the VELO state, windows (-1, -1).
 template <int G>
 __device__ __forceinline__ void not_searched(const FindArgs& A, uint32_t t, int gl) {
-    if (gl == 0) {
+    if (gl == 0 && !A.atomic_out && chk(t < A.n_tracks, A.status, 205)) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
         A.qop[t] = 0.f;
@@ -633,6 +657,7 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
     V.h = head;
     V.ft = ft;
     V.X = X;
+    V.st = A.status;
     V.off = off;
     V.S = S;
 #pragma unroll
@@ -643,7 +668,7 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
     const double u0 = __shfl_sync(gmask, mine.u, 0, G);
     const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= A.x_max);
 
-    if (gl == 0) {
+    if (gl == 0 && !A.atomic_out && chk(t < A.n_tracks, A.status, 205)) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
         A.qop[t] = 0.f;
@@ -683,7 +708,10 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
             if (G < 8 || gl < 4) {
                 while (a < b) {
                     const int m = (a + b) >> 1;
-                    if ((X[m] - uh) - ul >= -hw) b = m; else a = m + 1;
+                    if ((ld_chk(X, m, kChecked ? (long long)off[4 * S] : 0ll, A.status, 203) - uh) - ul >= -hw)
+                        b = m;
+                    else
+                        a = m + 1;
                 }
                 w0 = a;
                 b = rb;
@@ -691,7 +719,10 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
             if (G < 8 || gl >= 4) {
                 while (a < b) {
                     const int m = (a + b) >> 1;
-                    if ((X[m] - uh) - ul > hw) b = m; else a = m + 1;
+                    if ((ld_chk(X, m, kChecked ? (long long)off[4 * S] : 0ll, A.status, 203) - uh) - ul > hw)
+                        b = m;
+                    else
+                        a = m + 1;
                 }
                 w1 = a;
             }
@@ -703,6 +734,7 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
             head->sec0[l] = s0;
             head->cen[l] = c;
             head->scale[l] = w1 > w0 ? (float)(w1 - w0) / (2.f * hw) : 0.f;
+            head->hwt[l] = hw;
             head->hi[l] = uh;
             head->lo[l] = ul;
             if (A.kmap && gl == 0) {
@@ -723,7 +755,7 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
                 head->wsize[l][k] = size;
                 head->pre[l][k] = pre;
                 pre += size;
-                if (A.win) {
+                if (A.win && chk(t < A.n_tracks, A.status, 206)) {
                     int16_t* wp = A.win + (((size_t)t * 4 + l) * n_sec + k) * 2;
                     int16_t v0 = -1, v1 = -1;
                     if (size > 0) {
@@ -783,6 +815,8 @@ __device__ __forceinline__ void eval_queued(const FindArgs& A, GroupHead* wh, co
         V.h = h;
         V.ft = ft;
         V.X = X;
+        V.st = A.status;
+    V.st = A.status;
         V.off = off;
         V.S = A.S;
 #pragma unroll
@@ -858,6 +892,9 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             View V;
             V.h = h;
             V.X = X;
+            V.st = A.status;
+        V.st = A.status;
+    V.st = A.status;
             V.off = off;
             V.S = A.S;
             V.hi[la] = h->hi[la];
@@ -869,7 +906,7 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             float alo, ahi;
             kink_band_rev<DIR>(A, db, alo, ahi);
             const int wa1 = h->wunion[la][1];
-            p0 = V.lower(la, alo, A.hw[la]);
+            p0 = V.lower(la, alo, V.hw_hint(A, la));
             int p1 = p0;
             while (p1 < wa1 && V.d(la, p1) <= ahi) ++p1;
             c = p1 - p0;
@@ -896,7 +933,7 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             const int j_p0 = __shfl_sync(0xffffffffu, p0, j);
             const int j_ex = __shfl_sync(0xffffffffu, incl - c, j);
             const int m = min(32, n_pair - q0);
-            if (lane < m) {
+            if (lane < m && chk(nq + lane < kPairQ, A.status, 207)) {
                 Q->pa[nq + lane] = j_p0 + (q - j_ex);
                 Q->pb[nq + lane] = j_pb;
                 Q->u[nq + lane] = j_u;
@@ -997,6 +1034,7 @@ __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* f
     V.h = head;
     V.ft = ft;
     V.X = X;
+    V.st = A.status;
     V.off = off;
     V.S = A.S;
 #pragma unroll
@@ -1041,14 +1079,16 @@ __device__ void compass_warp(const FindArgs& A, GroupHead* wh, const FitTable* f
     } else {
         eval_pair_cold<1>(A, V, best_pa, best_pb, tk);
     }
+    const uint32_t r = output_row(A, e, t);
+    if (!chk(r < A.n_tracks, A.status, 204)) return;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = tk.pos[l] >= 0 ? (int)(hb + tk.pos[l]) : -1;
-    A.qop[t] = A.kmap ? tk.q * head->qscale : tk.q;
-    A.chi2[t] = tk.chi2;
-    A.xo[t] = vx + tk.a;
-    A.txo[t] = vtx + tk.b;
-    A.nhits[t] = (uint8_t)tk.nh;
-    A.found[t] = 1;
+    for (int l = 0; l < 4; ++l) A.hit[(size_t)r * 4 + l] = tk.pos[l] >= 0 ? (int)(hb + tk.pos[l]) : -1;
+    A.qop[r] = A.kmap ? tk.q * head->qscale : tk.q;
+    A.chi2[r] = tk.chi2;
+    A.xo[r] = vx + tk.a;
+    A.txo[r] = vtx + tk.b;
+    A.nhits[r] = (uint8_t)tk.nh;
+    A.found[r] = 1;
 }
 
 // Host: fill FindArgs (derived constants in float, one op per statement;

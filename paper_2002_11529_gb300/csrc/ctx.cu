@@ -38,9 +38,12 @@ extern "C" int ut_ctx_create(ut_ctx** out, const ut_geometry* geom) {
 
 extern "C" int ut_ctx_destroy(ut_ctx* c) {
     if (!c) return UT_ERR_ARG;
+    int cur = -1;
+    const bool swap = cudaGetDevice(&cur) == cudaSuccess && cur != c->device && cudaSetDevice(c->device) == cudaSuccess;
     if (c->d_kmap) cudaFree(c->d_kmap);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
+    if (swap) cudaSetDevice(cur);
     delete c;
     return UT_OK;
 }
@@ -59,13 +62,19 @@ extern "C" int ut_ctx_set_kick_map(ut_ctx* c, int nx, int ny, float tx_max, floa
         if (!(values[i] > 0.f) || !std::isfinite(values[i])) return UT_ERR_ARG;
         vmax = values[i] > vmax ? values[i] : vmax;
     }
+    // the map lives on the context's device, whichever device is current
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return UT_ERR_CUDA;
+    if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess) return UT_ERR_CUDA;
     float* d = nullptr;
-    if (cudaMalloc(&d, sizeof(float) * (size_t)nx * ny) != cudaSuccess) return UT_ERR_CUDA;
-    if (cudaMemcpy(d, values, sizeof(float) * (size_t)nx * ny, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d);
-        return UT_ERR_CUDA;
+    cudaError_t err = cudaMalloc(&d, sizeof(float) * (size_t)nx * ny);
+    if (err == cudaSuccess) {
+        err = cudaMemcpy(d, values, sizeof(float) * (size_t)nx * ny, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) cudaFree(d);
     }
-    if (c->d_kmap) cudaFree(c->d_kmap);
+    if (err == cudaSuccess && c->d_kmap) cudaFree(c->d_kmap);
+    if (cur != c->device) cudaSetDevice(cur);
+    if (err != cudaSuccess) return UT_ERR_CUDA;
     c->d_kmap = d;
     c->kmap_nx = nx;
     c->kmap_ny = ny;

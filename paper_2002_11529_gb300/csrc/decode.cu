@@ -280,7 +280,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // In host code `g_noalloc_scratch` is only a stand-in symbol, not a device
 // address: its device address is looked up once per device, with that
-// device current, and cached.
+// device current, and cached.  The cached address belongs to the device's
+// primary context: it is not valid after cudaDeviceReset (which ends that
+// context and unloads the library's device code).
 static std::mutex g_noalloc_mutex;
 static std::unordered_map<int, void*> g_noalloc_addr;
 
@@ -311,14 +313,16 @@ extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw,
     if (g.n_sectors < 1 || g.n_sectors > 4096 || g.strips < 1 || g.strips > 512 || !(g.sector_pitch > 0.f) ||
         !(g.strip_pitch > 0.f))
         return UT_ERR_ARG;
+    if (n_events > 0 && (!d_raw || !d_ev_off || !out->x || !out->z || !out->sector || !out->layer || !out->id))
+        return UT_ERR_ARG;
+    if (n_events > 0 && ((uintptr_t)d_raw & 15u) != 0) return UT_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != UT_OK) return rc;
+    // every host check has passed: only now is anything enqueued
     if (cudaMemsetAsync(d_status, 0xFF, sizeof(unsigned long long), st) != cudaSuccess) return UT_ERR_CUDA;
     if (n_events == 0) return check_cuda(cudaMemsetAsync(out->hit_off, 0, sizeof(uint32_t), st));
-    if (!d_raw || !d_ev_off || !out->x || !out->z || !out->sector || !out->layer || !out->id) return UT_ERR_ARG;
-    if (((uintptr_t)d_raw & 15u) != 0) return UT_ERR_ARG;
     const int S = g.n_sectors, B = 4 * S;
     DecodeArgs a;
     a.raw = d_raw;

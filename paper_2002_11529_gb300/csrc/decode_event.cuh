@@ -85,6 +85,7 @@ __device__ __forceinline__ float decode_x(const DecodeArgs& a, int s, uint32_t w
 
 __device__ __forceinline__ void write_hit(const DecodeArgs& a, uint32_t o, int l, int s, uint32_t w, float* sx,
                                           uint32_t sx_cap, uint32_t local) {
+    if (!chk(o < a.capacity, a.status, 101)) return;
     const float x = decode_x(a, s, w);
     a.x[o] = x;
     if (sx != nullptr && local < sx_cap) sx[local] = x;
@@ -308,7 +309,7 @@ __device__ __forceinline__ DecodedHit decoded_hit(const DecodeArgs& a, int b, ui
 // rank_big_banks straight into srcmap.
 template <bool SORT>
 __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total,
-                          bool any_big) {
+                          bool any_big, uint64_t nw) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int B = 4 * a.S;
     const uint32_t* off = sm.off;
@@ -319,7 +320,9 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
     };
     for (int b = tid; b < B; b += nt) {
         const uint32_t j0 = off[b], n = off[b + 1] - j0;
+        if (!chk(j0 + n <= a.map_cap, a.status, 104)) continue;
         if (SORT && n <= (uint32_t)kSmallBank) {
+            if (!chk((uint64_t)evw[b] + 1 + (n + 1) / 2 <= nw, a.status, 110)) continue;
             const uint32_t* w32 = evw + evw[b] + 1;  // two words per u32, low half first
             for (uint32_t k = 0; k < n; k += 2) {
                 const uint32_t v = w32[k >> 1];
@@ -359,6 +362,7 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
             const int b = (int)(v & 0x3FFu);
             const uint32_t o0 = off[b];
             if (off[b + 1] - o0 > (uint32_t)kSmallBank) continue;
+            if (!chk(o0 + (v >> 10) < a.map_cap, a.status, 105)) continue;
             srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
         }
         __syncthreads();
@@ -369,15 +373,19 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
 // start on a 16-byte boundary in global memory use vector stores.
 template <bool SORT>
 __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, const uint32_t* evw,
-                             unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap) {
+                             unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap,
+                             uint64_t nw) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const uint32_t* off = sm.off;
     const uint16_t* bmap = sm.bmap;
     const uint16_t* srcm = sm.srcmap;
     auto hit_at = [&](uint32_t o) -> DecodedHit {
-        const int b = SORT ? (int)(bmap[o] & 0x3FFu) : (int)bmap[o];
-        const uint32_t w = SORT ? (uint32_t)reinterpret_cast<const uint16_t*>(evw)[srcm[o]]
-                                : (uint32_t)bank_words(evw, b)[o - off[b]];
+        const int b = SORT ? (int)(ld_chk(bmap, o, a.map_cap, a.status, 107) & 0x3FFu)
+                           : (int)ld_chk(bmap, o, a.map_cap, a.status, 107);
+        const long long wpos = SORT ? (long long)ld_chk(srcm, o, a.map_cap, a.status, 107)
+                                    : 2ll * ((long long)evw[b] + 1) + (long long)(o - off[b]);
+        const uint32_t w = (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(evw), wpos, 2ll * (long long)nw,
+                                            a.status, 106);
         if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
         return decoded_hit(a, b, w);
     };
@@ -386,6 +394,7 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
         if (sx != nullptr && o < sx_cap) sx[o] = h.x;
         if (!fits) return;
         const size_t g = (size_t)(base + o);
+        if (!chk(g < a.capacity, a.status, 102)) return;
         a.x[g] = h.x;
         a.z[g] = h.z;
         a.sector[g] = (uint16_t)h.s;
@@ -406,6 +415,7 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
         }
         if (!fits) continue;
         const size_t g = (size_t)(base + o);
+        if (!chk(g + 4 <= a.capacity, a.status, 103)) continue;
         *reinterpret_cast<float4*>(a.x + g) = make_float4(h[0].x, h[1].x, h[2].x, h[3].x);
         *reinterpret_cast<float4*>(a.z + g) = make_float4(h[0].z, h[1].z, h[2].z, h[3].z);
         *reinterpret_cast<uint2*>(a.sector + g) = make_uint2(h[0].s | (h[1].s << 16), h[2].s | (h[3].s << 16));
@@ -506,7 +516,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
         st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
     // (sorted: bank and rank share 16 bits, word positions fit 16 bits)
     const bool mapped = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
-    if (mapped) map_event<SORT>(a, sm, evw, total, any_big);
+    if (mapped) map_event<SORT>(a, sm, evw, total, any_big, nw);
     if (tid < 32) {
         const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status, a.spin_limit) : 0ull;
         if (tid == 0) {
@@ -521,14 +531,15 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     if (!fits && tid == 0) report(a.status, UT_ERR_CAPACITY, -1, -1);
 
     uint32_t* hit_off = a.hit_off + (size_t)e * B;
-    for (int b = tid; b < B; b += nt) hit_off[b] = (uint32_t)(base + off[b]);
+    for (int b = tid; b < B; b += nt)
+        st_chk(hit_off, b, (long long)(a.n_events - e) * B + 1, (uint32_t)(base + off[b]), a.status, 108);
     if (e == a.n_events - 1 && tid == 0) a.hit_off[(size_t)a.n_events * B] = (uint32_t)end;
     if (!ev_ok) return;
 
     // Decode.  Mapped events are written in output order; larger ones use
     // one thread per hit (bank by binary search) writing at its ranked slot.
     if (mapped) {
-        write_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap);
+        write_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap, nw);
         return;
     }
     for (uint32_t i = tid; i < total; i += nt) {
@@ -536,7 +547,8 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
         const uint32_t k = i - off[b];
         const uint32_t n = off[b + 1] - off[b];
         const uint16_t* w16 = bank_words(evw, b);
-        const uint32_t w = w16[k];
+        const uint32_t w = ld_chk(reinterpret_cast<const uint16_t*>(evw), 2ll * ((long long)evw[b] + 1) + k,
+                                  2ll * (long long)nw, a.status, 109);
         if ((w & 0x3FFu) >= (uint32_t)a.strips) report(a.status, UT_ERR_STRIP, e, b);
         uint32_t r = k;
         if (SORT) {

@@ -34,6 +34,7 @@ struct GroupSearchArgs {
     const float* gyb;
     const float* gye;
     const uint32_t* goff;        // E * 4 * NG + 1
+    uint32_t capacity;           // entries of gx, gyb, gye
     int NG;
     float tol_y;
     uint32_t x_cap;
@@ -53,8 +54,12 @@ struct GsView {
     const GsTrack* T;
     const float* X;
     int n_sec;
+    uint32_t nX;                 // hits of the event readable through X
+    unsigned long long* st;      // status word (bounds-checked builds)
 
-    __device__ __forceinline__ float d(int l, int p) const { return (X[p] - T->hi[l]) - T->lo[l]; }
+    __device__ __forceinline__ float d(int l, int p) const {
+        return (ld_chk(X, p, (long long)nX, st, 301) - T->hi[l]) - T->lo[l];
+    }
     __device__ __forceinline__ bool in_x(int l, float v) const { return v >= -T->hw[l] && v <= T->hw[l]; }
     // position of y-window hit ri (0 <= ri < len[l]) of layer l, slot order
     __device__ __forceinline__ int pos(int l, int ri) const {
@@ -201,11 +206,11 @@ __device__ int gs_direction(const FindArgs& A, const GsView& V, const FitTable* 
 
 // The whole search of VELO track t of event e by one warp.
 __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T, const FitTable* ft, const float* X,
-                         const uint32_t* soff, const float* sedge, uint32_t h0, int e, uint32_t t, bool search,
-                         int lane) {
+                         const uint32_t* soff, const float* sedge, uint32_t h0, uint32_t nX, int e, uint32_t t,
+                         bool search, int lane) {
     __syncwarp();  // the previous track's reads of *T are done
     const float vx = A.vx[t], vy = A.vy[t], vtx = A.vtx[t], vty = A.vty[t];
-    if (lane == 0) {
+    if (lane == 0 && !A.atomic_out && chk(t < A.n_tracks, A.status, 303)) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = -1;
         A.qop[t] = 0.f;
@@ -266,13 +271,13 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
                 uint32_t lo_ = a, hi_ = b;
                 while (lo_ < hi_) {
                     const uint32_t m = lo_ + (hi_ - lo_) / 2;
-                    if (__ldg(G.gye + m) >= ylo) hi_ = m; else lo_ = m + 1;
+                    if (ld_chk(G.gye, m, G.capacity, A.status, 302) >= ylo) hi_ = m; else lo_ = m + 1;
                 }
                 const uint32_t q0 = lo_;
                 hi_ = b;
                 while (lo_ < hi_) {
                     const uint32_t m = lo_ + (hi_ - lo_) / 2;
-                    if (__ldg(G.gyb + m) > yhi) hi_ = m; else lo_ = m + 1;
+                    if (ld_chk(G.gyb, m, G.capacity, A.status, 302) > yhi) hi_ = m; else lo_ = m + 1;
                 }
                 j0 = (int)(q0 - h0);
                 j1 = (int)(lo_ - h0);
@@ -294,6 +299,8 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
     V.T = T;
     V.X = X;
     V.n_sec = A.n_sec;
+    V.nX = nX;
+    V.st = A.status;
     // some layer has a candidate (a y-window hit inside its x window)
     bool any = false;
     for (int l = 0; l < 4 && !any; ++l)
@@ -328,14 +335,16 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
         }
     }
     if (k_nh == 0 || lane != k_lane) return;
+    const uint32_t r = output_row(A, e, t);
+    if (!chk(r < A.n_tracks, A.status, 303)) return;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) A.hit[(size_t)t * 4 + l] = l_tk.pos[l] >= 0 ? (int)(h0 + (uint32_t)l_tk.pos[l]) : -1;
-    A.qop[t] = A.kmap ? l_tk.q * (A.kick_k / kick) : l_tk.q;
-    A.chi2[t] = l_tk.chi2;
-    A.xo[t] = vx + l_tk.a;
-    A.txo[t] = vtx + l_tk.b;
-    A.nhits[t] = (uint8_t)l_tk.nh;
-    A.found[t] = 1;
+    for (int l = 0; l < 4; ++l) A.hit[(size_t)r * 4 + l] = l_tk.pos[l] >= 0 ? (int)(h0 + (uint32_t)l_tk.pos[l]) : -1;
+    A.qop[r] = A.kmap ? l_tk.q * (A.kick_k / kick) : l_tk.q;
+    A.chi2[r] = l_tk.chi2;
+    A.xo[r] = vx + l_tk.a;
+    A.txo[r] = vtx + l_tk.b;
+    A.nhits[r] = (uint8_t)l_tk.nh;
+    A.found[r] = 1;
 }
 
 __global__ void __launch_bounds__(kGsThreads) compass_groups_kernel(const FindArgs A, const GroupSearchArgs G) {
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(kGsThreads) compass_groups_kernel(const FindAr
     const bool search = A.gec == 0 || n <= (uint32_t)A.gec;  // Global Event Cut (Sec. VI)
     const uint32_t t0 = A.trk_off[e], tn = A.trk_off[e + 1] - t0;
     for (uint32_t k = (uint32_t)w; k < tn; k += (uint32_t)W)
-        gs_track(A, G, trk + w, ft, X, soff, sedge, h0, e, t0 + k, search, lane);
+        gs_track(A, G, trk + w, ft, X, soff, sedge, h0, n, e, t0 + k, search, lane);
 }
 
 }  // namespace utc
@@ -391,12 +400,17 @@ extern "C" int compass_find_groups(ut_ctx* ctx, const ut_group_hits* hits, const
     FindArgs A;
     const int rc = make_find_args(&cg, &hx, velo, n_events, n_tracks, p, out, nullptr, A);
     if (rc != UT_OK) return rc;
-    if (n_events == 0 || n_tracks == 0) return UT_OK;
+    if (n_events == 0) return UT_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (A.atomic_out && cudaMemsetAsync(out->n_found, 0, sizeof(uint32_t) * (size_t)n_events, st) != cudaSuccess)
+        return UT_ERR_CUDA;
+    if (n_tracks == 0) return UT_OK;
     GroupSearchArgs G;
     G.gx = hits->x;
     G.gyb = hits->y_begin;
     G.gye = hits->y_end;
     G.goff = hits->group_off;
+    G.capacity = hits->capacity;
     G.NG = gg->n_groups;
     G.tol_y = tol_y;
     G.x_cap = kGsXCap;
@@ -407,7 +421,6 @@ extern "C" int compass_find_groups(ut_ctx* ctx, const ut_group_hits* hits, const
     if (cudaFuncSetAttribute(compass_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return UT_ERR_CUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     compass_groups_kernel<<<n_events, kGsThreads, smem, st>>>(A, G);
     return check_cuda(cudaGetLastError());
 }

@@ -203,7 +203,7 @@ static void launch_request(ut_server* sv, Slot& sl, Request* q) {
     velo.ty = reinterpret_cast<const float*>(base + L.vty);
     velo.flags = reinterpret_cast<const uint8_t*>(base + L.flags);
     velo.trk_off = reinterpret_cast<const uint32_t*>(base + L.trk_off);
-    compass_tracks tr;
+    compass_tracks tr{};
     tr.hit = reinterpret_cast<int32_t*>(base + L.hit);
     tr.qop = reinterpret_cast<float*>(base + L.qop);
     tr.chi2 = reinterpret_cast<float*>(base + L.chi2);
@@ -321,6 +321,7 @@ extern "C" size_t ut_server_request_bytes(const ut_geometry* geom, const ut_serv
 extern "C" int ut_server_create(ut_server** out, const ut_geometry* geom, const compass_params* p,
                                 size_t budget_bytes, int n_slots, const ut_launch_config* cfg) {
     if (!out || !geom || !p || n_slots < 1 || n_slots > 64 || budget_bytes < 4096) return UT_ERR_ARG;
+    if (p->output_order != 0) return UT_ERR_ARG;  // request outputs are per VELO slot
     *out = nullptr;
     ut_server* sv = new (std::nothrow) ut_server();
     if (!sv) return UT_ERR_ARG;

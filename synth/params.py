@@ -15,6 +15,9 @@ choices for the synthetic detector:
 * gec_max_hits: the Global Event Cut applied before the tracking (Sec. VI):
   events with more UT hits are not searched; 0 = no cut.  The paper takes
   LHCb's cut and gives no value.
+* output_order: 0 = each VELO track's result in its own slot; 1 = the
+  paper's output order (found tracks of an event at indices taken from an
+  atomic counter, Sec. V-B).  Not an input of the method's arithmetic.
 """
 from __future__ import annotations
 
@@ -38,6 +41,7 @@ class CompassParams:
     z_kink: float = 2500.0
     kick_k: float = 1.2
     gec_max_hits: int = 0
+    output_order: int = 0
 
     def replace(self, **kw) -> "CompassParams":
         return dataclasses.replace(self, **kw)

@@ -170,3 +170,47 @@ def test_twenty_steps_recover_the_injected_offsets(g):
           f"truth {c_true / a.n_tracks:.4f}; within 3 sigma: {frac:.4f}; "
           f"rms error {np.sqrt((err.reshape(-1, 3) ** 2).mean(0))}")
     assert frac >= 0.95
+
+
+def _host_pcg(prob, a0, steps):
+    """The same preconditioned CG on the host in float64 (numpy), with the
+    library's refit, chi2 blocks and Hessian-vector product as the
+    operators: the reference for the device loop's own arithmetic."""
+    th = prob.refit(a0)
+    _, _, g, h = prob.chi2(th, a0, grads=True)
+    g = g.cpu().numpy().astype(np.float64)
+    h = h.cpu().numpy().astype(np.float64)
+    minv = np.zeros((h.shape[0], 3, 3))
+    for s, (a, b, c, d, e, f) in enumerate(h):
+        m = np.array([[a, b, c], [b, d, e], [c, e, f]])
+        if a > 0 and np.linalg.det(m) != 0:
+            minv[s] = np.linalg.inv(m)
+    r = -g
+    z = np.einsum("sij,sj->si", minv, r)
+    p = z.copy()
+    x = np.zeros_like(r)
+    rz = (r * z).sum()
+    for _ in range(steps):
+        ap = prob.hvp(th, a0, torch.from_numpy(p).cuda()).cpu().numpy()
+        alpha = rz / (p * ap).sum()
+        x += alpha * p
+        r -= alpha * ap
+        z = np.einsum("sij,sj->si", minv, r)
+        rz_new = (r * z).sum()
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return (a0.cpu().numpy().astype(np.float64) + x)
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+def test_device_solver_steps_match_host_cg(g, medium, steps):
+    """ut_align_solve's CG steps (one linearisation) equal the same steps
+    done on the host in float64 with the library's operators."""
+    from paper_2002_11529_gb300.align import solve_alignment
+    a, prob, _ = medium
+    a0 = torch.zeros((4 * prob.S, 3), dtype=torch.float32, device="cuda")
+    est, hist = solve_alignment(prob, steps=steps, relinearize_every=steps)
+    ref = _host_pcg(prob, a0, steps)
+    assert close(est.cpu().numpy().astype(np.float64), ref, rtol=1e-4)
+    h = hist.cpu().numpy()
+    assert h.shape == (2,) and h[1] < h[0]

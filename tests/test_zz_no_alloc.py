@@ -6,13 +6,15 @@ cudaMalloc's implicit synchronisation).  This entry point takes no
 workspace and no context: its scratch is a static device array of the
 library.  These tests call it through the C ABI and compare its output with
 ut_decode's, bit for bit, on two calls in a row (the second on a smaller
-batch, so stale scratch from the first call must not leak into it).
+batch, so stale scratch from the first call must not leak into it), and
+with the CPU oracle's decode.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 
@@ -55,7 +57,36 @@ def test_noalloc_decode_matches_ut_decode_twice():
             assert n == b.n_hits
             for k in ("x", "z", "sector", "layer", "id"):
                 assert np.array_equal(r[k][:n].view(np.uint8), o[k][:n].view(np.uint8)), k
+            # and the oracle's decode, directly
+            rc, oh, _ = oracle.decode(b.raw, b.ev_off, b.n_events, geom, sorted_)
+            assert rc == 0
+            assert np.array_equal(o["hit_off"], oh.hit_off)
+            assert np.array_equal(o["x"][:n].view(np.uint32), oh.x[:n].view(np.uint32))
+            assert np.array_equal(o["id"][:n], oh.id[:n])
     ctx.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_argument_error_enqueues_nothing():
+    """A call refused by a host check (a null output array) returns
+    UT_ERR_ARG without writing the caller's status word."""
+    import torch
+    import paper_2002_11529_gb300 as g
+    g.build.build()
+    b = synth.generate_config("tiny")
+    raw, ev = g.upload_raw(b.raw, b.ev_off)
+    nw = int(b.ev_off[-1])
+    out = g.HitBuffers.allocate(2 * nw, b.n_events, b.geom.n_sectors)
+    h = out.struct()
+    h.z = None
+    status = torch.full((1,), 1234, dtype=torch.int64, device="cuda")
+    geo = g.geometry_struct(b.geom)
+    rc = g.lib().ut_decode_noalloc(ctypes.byref(geo), ctypes.c_void_p(raw.data_ptr()), nw,
+                                   ctypes.c_void_p(ev.data_ptr()), b.n_events, ctypes.byref(h), 1,
+                                   ctypes.c_void_p(status.data_ptr()), None)
+    assert rc == g.UT_ERR_ARG
+    torch.cuda.synchronize()
+    assert int(status.item()) == 1234
 
 
 @pytest.mark.gpu
