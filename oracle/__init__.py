@@ -83,6 +83,8 @@ def lib():
             _lib.orc_group_candidates.restype = ctypes.c_int
             _lib.orc_group_candidates.argtypes = [P, P, P, P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P, P,
                                                   P, ctypes.c_float, ctypes.c_int, P, P]
+            _lib.orc_extrapolate.restype = None
+            _lib.orc_extrapolate.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P]
             _lib.orc_kick_at.restype = ctypes.c_float
             _lib.orc_kick_at.argtypes = [P, ctypes.c_float, ctypes.c_float]
             _lib.orc_align_chi2.restype = ctypes.c_int
@@ -495,3 +497,14 @@ def group_candidates(gh, batch, params, tol_y=10.0, kick_map=None, max_cand=4096
     if rc != 0:
         raise OracleError(rc, -1)
     return cand[:T], n[:T]
+
+
+def extrapolate(geom, vx, vy, vtx, vty):
+    """The oracle's prediction of a VELO track in the four layers
+    (orc_extrapolate): float32 arrays hi[4], lo[4]."""
+    g = geom_struct(geom)
+    hi = np.zeros(4, np.float32)
+    lo = np.zeros(4, np.float32)
+    lib().orc_extrapolate(ctypes.byref(g), ctypes.c_float(vx), ctypes.c_float(vy), ctypes.c_float(vtx),
+                          ctypes.c_float(vty), _p(hi), _p(lo))
+    return hi, lo

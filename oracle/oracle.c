@@ -438,20 +438,59 @@ int orc_fit64_d(const double* d, const int* present, const double* t, const doub
     return 1;
 }
 
+/* Error-free float transformations (Knuth's TwoSum, and TwoProd with a
+ * correctly rounded fused multiply-add): a + b = s + e and a * b = p + e
+ * exactly, s, p the rounded results. */
+static void two_sum(float a, float b, float* s, float* e) {
+    const float t = a + b;
+    const float bb = t - a;
+    *e = (a - (t - bb)) + (b - bb);
+    *s = t;
+}
+
+static void two_prod(float a, float b, float* p, float* e) {
+    const float t = a * b;
+    *e = fmaf(a, b, -t);
+    *p = t;
+}
+
 /* Straight VELO extrapolation to layer l in the measured coordinate
- * u_l = x_v(z_l) - y_v(z_l) tan(a_l), in double from the float state, and
- * its split into a float pair (hi, lo) so that a float residual
- * d = (x - hi) - lo keeps the accuracy of the double prediction. */
+ * u_l = x_v(z_l) - y_v(z_l) tan(a_l) (Sec. V-A), from the float state, as a
+ * float pair (hi, lo) carrying about twice the float precision, so that a
+ * float residual d = (x - hi) - lo keeps that accuracy: dz = z_l - z_velo
+ * (float); x_v = x + tx dz and y_v = y + ty dz each as TwoProd + TwoSum with
+ * the two errors added; y_v tan(a_l) as TwoProd of the leading part plus the
+ * trailing part times tan; u = TwoSum of the leading parts plus the
+ * trailing ones; then renormalised (hi = s + e, lo = e - (hi - s)).  Float
+ * operations only, in this order.  u[l] = (double)hi + (double)lo is the
+ * value every decision in double uses (acceptance, sector and group
+ * choice, the double fit). */
 static void extrapolate(const orc_geom* g, float vx, float vy, float vtx, float vty,
                         double* u, float* uhi, float* ulo) {
     for (int l = 0; l < 4; ++l) {
-        double dz = (double)g->z[l] - (double)g->z_velo;
-        double xv = (double)vx + (double)vtx * dz;
-        double yv = (double)vy + (double)vty * dz;
-        u[l] = xv - yv * (double)g->tan_a[l];
-        uhi[l] = (float)u[l];
-        ulo[l] = (float)(u[l] - (double)uhi[l]);
+        const float dz = g->z[l] - g->z_velo;
+        float p, ep, xs, xe, py, epy, ys, ye, q, eq, h0, e0;
+        two_prod(vtx, dz, &p, &ep);
+        two_sum(vx, p, &xs, &xe);
+        const float xl = xe + ep;
+        two_prod(vty, dz, &py, &epy);
+        two_sum(vy, py, &ys, &ye);
+        const float yl = ye + epy;
+        two_prod(ys, g->tan_a[l], &q, &eq);
+        const float ql = eq + yl * g->tan_a[l];
+        two_sum(xs, -q, &h0, &e0);
+        const float lo0 = e0 + (xl - ql);
+        const float hi = h0 + lo0;
+        uhi[l] = hi;
+        ulo[l] = lo0 - (hi - h0);
+        u[l] = (double)uhi[l] + (double)ulo[l];
     }
+}
+
+/* The extrapolation on its own (exposed for tests): hi, lo of layer l. */
+void orc_extrapolate(const orc_geom* g, float vx, float vy, float vtx, float vty, float* uhi, float* ulo) {
+    double u[4];
+    extrapolate(g, vx, vy, vtx, vty, u, uhi, ulo);
 }
 
 typedef struct {

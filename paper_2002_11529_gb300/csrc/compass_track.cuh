@@ -117,30 +117,65 @@ __device__ __forceinline__ float kick_at(const FindArgs& A, float tx, float ty) 
     return r0 + ay * (r1 - r0);
 }
 
-// Track prediction in the measured coordinate of layer l:
-// u_l = x_v(z_l) - y_v(z_l) * tan(a_l) in double, split into (hi, lo).
+// Error-free float transformations: a + b = s + e (Knuth's TwoSum) and
+// a * b = p + e (TwoProd with a correctly rounded fused multiply-add),
+// exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    const float t = __fadd_rn(a, b);
+    const float bb = __fsub_rn(t, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+    s = t;
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    const float t = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -t);
+    p = t;
+}
+
+// Track prediction in the measured coordinate of layer l (Sec. V-A):
+// u_l = x_v(z_l) - y_v(z_l) tan(a_l) as a float pair (hi, lo) of about twice
+// the float precision, float operations only: dz = z_l - z_velo; x_v and
+// y_v each by TwoProd + TwoSum with the errors added; y_v tan(a_l) by
+// TwoProd of the leading part plus the trailing part times tan; u by
+// TwoSum of the leading parts plus the trailing ones; renormalised.
 struct LayerPred {
     float hi, lo;
     int c;        // central sector (clamped)
-    double u;
 };
+
+__device__ __forceinline__ void predict_pair(const FindArgs& a, float vx, float vy, float vtx, float vty, int l,
+                                             float& hi, float& lo) {
+    const float dz = __fsub_rn(a.z[l], a.z_velo);
+    float p, ep, xs, xe, py, epy, ys, ye, q, eq, h0, e0;
+    two_prod(vtx, dz, p, ep);
+    two_sum(vx, p, xs, xe);
+    const float xl = __fadd_rn(xe, ep);
+    two_prod(vty, dz, py, epy);
+    two_sum(vy, py, ys, ye);
+    const float yl = __fadd_rn(ye, epy);
+    two_prod(ys, a.tan_a[l], q, eq);
+    const float ql = __fadd_rn(eq, __fmul_rn(yl, a.tan_a[l]));
+    two_sum(xs, -q, h0, e0);
+    const float lo0 = __fadd_rn(e0, __fsub_rn(xl, ql));
+    hi = __fadd_rn(h0, lo0);
+    lo = __fsub_rn(lo0, __fsub_rn(hi, h0));
+}
 
 __device__ __forceinline__ LayerPred predict(const FindArgs& a, float vx, float vy, float vtx, float vty, int l) {
     LayerPred p;
-    const double dz = (double)a.z[l] - (double)a.z_velo;
-    const double xv = (double)vx + (double)vtx * dz;
-    const double yv = (double)vy + (double)vty * dz;
-    p.u = xv - yv * (double)a.tan_a[l];
-    p.hi = (float)p.u;
-    p.lo = (float)(p.u - (double)p.hi);
-    // central sector floor((u - x_min) / pitch) in double, clamped; a float
-    // estimate decides whenever it is farther than 1e-3 + 1e-5 |q| from an
-    // integer, far above its error (a few 1e-7 of |q| + |x_min| / pitch)
+    predict_pair(a, vx, vy, vtx, vty, l, p.hi, p.lo);
+    // central sector floor((u - x_min) / pitch), u = hi + lo in double,
+    // clamped; a float estimate decides whenever it is farther than
+    // 1e-3 + 1e-5 |q| from an integer, far above its error (a few 1e-7 of
+    // |q| + |x_min| / pitch); only the rare cases near a sector edge take the
+    // double division
     const float qf = __fmul_rn(__fsub_rn(p.hi, a.x_min), a.inv_pitch);
     if (fabsf(__fsub_rn(qf, rintf(qf))) >= __fadd_rn(1e-3f, __fmul_rn(1e-5f, fabsf(qf)))) {
         p.c = (int)fminf(fmaxf(floorf(qf), 0.f), (float)(a.S - 1));
     } else {
-        const double q = (p.u - (double)a.x_min) / (double)a.pitch;
+        const double u = (double)p.hi + (double)p.lo;
+        const double q = (u - (double)a.x_min) / (double)a.pitch;
         const double fq = fmin(fmax(floor(q), 0.0), (double)(a.S - 1));
         p.c = (int)fq;
     }
@@ -652,7 +687,6 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
     LayerPred mine;
     mine.hi = mine.lo = 0.f;
     mine.c = 0;
-    mine.u = 0.0;
     if (gl < 4) mine = predict(A, vx, vy, vtx, vty, gl);
     V.h = head;
     V.ft = ft;
@@ -665,7 +699,8 @@ __device__ __forceinline__ bool setup_track(const FindArgs& A, GroupHead* head, 
         V.hi[l] = __shfl_sync(gmask, mine.hi, l, G);
         V.lo[l] = __shfl_sync(gmask, mine.lo, l, G);
     }
-    const double u0 = __shfl_sync(gmask, mine.u, 0, G);
+    // acceptance (Sec. V-A) on u_0 = hi + lo in double
+    const double u0 = (double)V.hi[0] + (double)V.lo[0];
     const bool accept = !backward && (u0 >= (double)A.x_min && u0 <= A.x_max);
 
     if (gl == 0 && !A.atomic_out && chk(t < A.n_tracks, A.status, 205)) {

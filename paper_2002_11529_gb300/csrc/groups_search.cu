@@ -227,13 +227,10 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
     int c = 0;
     const int NG = G.NG;
     if (lane < 4) {
+        predict_pair(A, vx, vy, vtx, vty, lane, hi, lo);
+        u = (double)hi + (double)lo;
         const double dz = (double)A.z[lane] - (double)A.z_velo;
-        const double xv = (double)vx + (double)vtx * dz;
-        const double yv = (double)vy + (double)vty * dz;
-        u = xv - yv * (double)A.tan_a[lane];
-        hi = (float)u;
-        lo = (float)(u - (double)hi);
-        y = (float)yv;
+        y = (float)((double)vy + (double)vty * dz);
         // c = number of interior edges k in [1, NG - 1] with edges[k] <= u
         int a = 1, b = NG;
         while (a < b) {

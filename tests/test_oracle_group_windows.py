@@ -28,7 +28,6 @@ def scan_candidates(gh, batch, params, tol_y, vy, vty):
     x_min = f64(f32(gg.x_min))
     x_max = x_min + f64(S) * f64(f32(base.sector_pitch))
     z = np.asarray(base.z, f32)
-    tan_a = np.asarray(base.tan_stereo, f32)
     kq = f32(params.kick_k) * f32(params.qop_max)
     hw = [kq * f32(abs(f32(z[l]) - f32(params.z_kink))) + f32(params.tol_win) for l in range(4)]
     out = []
@@ -38,16 +37,10 @@ def scan_candidates(gh, batch, params, tol_y, vy, vty):
             if batch.velo_flags[tr] & 1:
                 out.append(lists)
                 continue
-            vx, vtx = f64(f32(batch.velo_x[tr])), f64(f32(batch.velo_tx[tr]))
             y0, ty = f64(f32(vy[tr])), f64(f32(vty[tr]))
-            u, hi, lo = [], [], []
-            for l in range(4):
-                dz = f64(z[l]) - f64(f32(base.z_velo))
-                ul = (vx + vtx * dz) - (y0 + ty * dz) * f64(tan_a[l])
-                h = f32(ul)
-                u.append(ul)
-                hi.append(h)
-                lo.append(f32(ul - f64(h)))
+            # the prediction (pinned on its own in test_oracle_extrapolate.py)
+            hi, lo = oracle.extrapolate(base, batch.velo_x[tr], vy[tr], batch.velo_tx[tr], vty[tr])
+            u = [f64(hi[l]) + f64(lo[l]) for l in range(4)]
             if not (x_min <= u[0] <= x_max):
                 out.append(lists)
                 continue
