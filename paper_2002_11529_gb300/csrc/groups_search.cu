@@ -7,12 +7,15 @@
 // 0-3 extrapolate the track to the four layers (double) and pick the group
 // holding each prediction; lane 5 l + k runs the two y binary searches of
 // slot group k of layer l.  A layer's candidates are the hits of its y
-// windows, in slot order then storage order, that pass the x window; they
-// are never listed: the warp walks the y windows.  The tracklet search keeps
-// the sequential enumeration order exactly: the first anchor advances one
-// candidate at a time (the same for every lane), the second-anchor
-// candidates are taken 32 y-window hits at a time (lane i the i-th hit,
-// its candidate index from a ballot prefix), so the pairs of one step are
+// windows, in slot order then storage order, that pass the x window.  The
+// warp lists them (position and residual, by a ballot prefix over 32
+// y-window hits at a time) in its shared memory; the tracklet search then
+// deals the (first, second) anchor pairs to the lanes 32 at a time in their
+// sequential (lexicographic) order, and collection scans the listed
+// residuals.  A track with more than kGsListCap candidates in a layer keeps
+// the unlisted form: the first anchor advances one candidate at a time (the
+// same for every lane) while the second-anchor candidates are taken 32
+// y-window hits at a time.  Either way the pairs of one step are
 // consecutive in (first, second) order; the valid tracklets of a step are
 // ranked by a ballot prefix and only the first n_candidates of the
 // direction take part in the selection.  Every decision is the float
@@ -48,6 +51,15 @@ struct GsTrack {
     int r0[4][kMaxSectors], r1[4][kMaxSectors];
     int len[4];
     float hi[4], lo[4], hw[4];
+};
+
+// The listed candidates of the warp's track: per layer, in candidate order,
+// the event-local position and the residual d.
+constexpr int kGsListCap = 64;
+struct GsList {
+    int n[4];
+    int pos[4][kGsListCap];
+    float d[4][kGsListCap];
 };
 
 struct GsView {
@@ -204,8 +216,150 @@ __device__ int gs_direction(const FindArgs& A, const GsView& V, const FitTable* 
     return count < A.n_cand ? count : A.n_cand;
 }
 
+// Collection over a listed layer: the candidate nearest `pred` within
+// tol_col, ties to the earliest.
+__device__ __forceinline__ int gs_collect_list(const FindArgs& A, const GsList* Lc, int l, float pred, float& dsel) {
+    int bi = -1;
+    float bd = 0.f;
+    const int n = Lc->n[l];
+    for (int i = 0; i < n; ++i) {
+        const float dv = Lc->d[l][i];
+        const float dist = fabsf(dv - pred);
+        if (!(dist <= A.tol_col)) continue;
+        if (bi < 0 || dist < bd) {
+            bi = i;
+            bd = dist;
+            dsel = dv;
+        }
+    }
+    return bi < 0 ? -1 : Lc->pos[l][bi];
+}
+
+// The anchor pair (da, db) of direction DIR over listed candidates: the
+// operations of gs_eval.
+template <int DIR>
+__device__ __forceinline__ bool gs_eval_list(const FindArgs& A, const GsList* Lc, const FitTable* ft, float stol,
+                                             int pos_a, int pos_b, float da, float db, Tracklet& out) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    constexpr int lc0 = DIR ? 2 : 1, lc1 = DIR ? 0 : 3;
+    const float dzab = A.z[lb] - A.z[la];
+    const float dzk = A.z_kink - A.z[la];
+    const float sr = (db - da) / dzab;
+    if (!(fabsf(sr) <= stol)) return false;
+    const float dk = da + sr * dzk;
+    if (!(fabsf(dk) <= A.tol_kink)) return false;
+    float dl[4] = {0.f, 0.f, 0.f, 0.f};
+    bool present[4] = {false, false, false, false};
+    out.pos[0] = out.pos[1] = out.pos[2] = out.pos[3] = -1;
+    dl[la] = da;
+    present[la] = true;
+    out.pos[la] = pos_a;
+    dl[lb] = db;
+    present[lb] = true;
+    out.pos[lb] = pos_b;
+    int nh = 2;
+    {
+        const float pred = da + sr * (A.z[lc0] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = gs_collect_list(A, Lc, lc0, pred, dsel);
+        if (bi >= 0) {
+            dl[lc0] = dsel;
+            present[lc0] = true;
+            out.pos[lc0] = bi;
+            ++nh;
+        }
+    }
+    {
+        const float pred = da + sr * (A.z[lc1] - A.z[la]);
+        float dsel = 0.f;
+        const int bi = gs_collect_list(A, Lc, lc1, pred, dsel);
+        if (bi >= 0) {
+            dl[lc1] = dsel;
+            present[lc1] = true;
+            out.pos[lc1] = bi;
+            ++nh;
+        }
+    }
+    if (nh < 3) return false;
+    float fa, fb, fq, c2;
+    if (!fit32(dl, present, A, ft, fa, fb, fq, c2)) return false;
+    const float c2n = c2 / (float)(nh - 1);
+    if (!(c2n <= A.chi2ndof_max)) return false;
+    out.nh = nh;
+    out.chi2 = c2;
+    out.a = fa;
+    out.b = fb;
+    out.q = fq;
+    return true;
+}
+
+// One direction over listed candidates: pair q = ia * nb + ib (the
+// sequential order) is taken by lane q % 32 of step q / 32.
+template <int DIR>
+__device__ int gs_direction_list(const FindArgs& A, const GsList* Lc, const FitTable* ft, float stol, int lane,
+                                 int& l_nh, float& l_c2, unsigned long long& l_key, Tracklet& l_tk) {
+    constexpr int la = DIR ? 3 : 0, lb = DIR ? 1 : 2;
+    const int na = Lc->n[la], nb = Lc->n[lb];
+    const int np = na * nb;
+    int count = 0;
+    for (int q0 = 0; q0 < np && count < A.n_cand; q0 += 32) {
+        const int q = q0 + lane;
+        bool valid = false;
+        Tracklet tk;
+        if (q < np) {
+            const int ia = q / nb, ib = q - ia * nb;
+            valid = gs_eval_list<DIR>(A, Lc, ft, stol, Lc->pos[la][ia], Lc->pos[lb][ib], Lc->d[la][ia], Lc->d[lb][ib],
+                                      tk);
+        }
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        if (valid && count + __popc(vm & lanemask_lt()) < A.n_cand) {
+            if (l_nh == 0 || tk.nh > l_nh || (tk.nh == l_nh && tk.chi2 < l_c2)) {
+                l_nh = tk.nh;
+                l_c2 = tk.chi2;
+                l_key = (unsigned long long)q;
+                l_tk = tk;
+            }
+        }
+        count += __popc(vm);
+    }
+    return count < A.n_cand ? count : A.n_cand;
+}
+
+// Lists the candidates of every layer (ballot prefix over 32 y-window hits
+// at a time); returns false when a layer has more than kGsListCap.
+__device__ __forceinline__ bool gs_list(const GsView& V, GsList* Lc, int lane) {
+    bool ok = true;
+    for (int l = 0; l < 4; ++l) {
+        const int len = V.T->len[l];
+        int n = 0;
+        for (int r0 = 0; r0 < len; r0 += 32) {
+            const int ri = r0 + lane;
+            int p = -1;
+            float dv = 0.f;
+            bool c = false;
+            if (ri < len) {
+                p = V.pos(l, ri);
+                dv = V.d(l, p);
+                c = V.in_x(l, dv);
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, c);
+            const int k = n + __popc(m & lanemask_lt());
+            if (c && k < kGsListCap) {
+                Lc->pos[l][k] = p;
+                Lc->d[l][k] = dv;
+            }
+            n += __popc(m);
+        }
+        if (lane == 0) Lc->n[l] = n < kGsListCap ? n : kGsListCap;
+        ok = ok && n <= kGsListCap;
+    }
+    __syncwarp();
+    return ok;
+}
+
 // The whole search of VELO track t of event e by one warp.
-__device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T, const FitTable* ft, const float* X,
+__device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T, GsList* Lc, const FitTable* ft,
+                         const float* X,
                          const uint32_t* soff, const float* sedge, uint32_t h0, uint32_t nX, int e, uint32_t t,
                          bool search, int lane) {
     __syncwarp();  // the previous track's reads of *T are done
@@ -298,22 +452,21 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
     V.n_sec = A.n_sec;
     V.nX = nX;
     V.st = A.status;
-    // some layer has a candidate (a y-window hit inside its x window)
-    bool any = false;
-    for (int l = 0; l < 4 && !any; ++l)
-        for (int r = lane; r < T->len[l]; r += 32)
-            if (V.in_x(l, V.d(l, V.pos(l, r)))) {
-                any = true;
-                break;
-            }
-    if (!__any_sync(0xffffffffu, any)) return;
     const float stol = A.kmap ? kqt + A.tol_slope : A.slope_tol;
     int l_nh = 0;
     float l_c2 = 0.f;
     unsigned long long l_key = ~0ull;
     Tracklet l_tk;
-    int count = gs_direction<0>(A, V, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
-    if (count == 0) gs_direction<1>(A, V, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
+    if (gs_list(V, Lc, lane)) {
+        // listed candidates; searched when some layer has one
+        if (Lc->n[0] + Lc->n[1] + Lc->n[2] + Lc->n[3] == 0) return;
+        const int count = gs_direction_list<0>(A, Lc, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
+        if (count == 0) gs_direction_list<1>(A, Lc, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
+    } else {
+        // more candidates than a list holds: walk the y windows
+        const int count = gs_direction<0>(A, V, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
+        if (count == 0) gs_direction<1>(A, V, ft, stol, lane, l_nh, l_c2, l_key, l_tk);
+    }
     // the best over the lanes: most hits, lowest chi2, earliest
     int k_nh = l_nh, k_lane = lane;
     float k_c2 = l_c2;
@@ -353,7 +506,8 @@ __global__ void __launch_bounds__(kGsThreads) compass_groups_kernel(const FindAr
     FitTable* ft = reinterpret_cast<FitTable*>(reinterpret_cast<unsigned char*>(sedge) +
                                                (((size_t)(NG + 1) * 4 + 15) & ~(size_t)15));
     GsTrack* trk = reinterpret_cast<GsTrack*>(ft + 1);
-    float* sx = reinterpret_cast<float*>(trk + W);
+    GsList* lists = reinterpret_cast<GsList*>(trk + W);
+    float* sx = reinterpret_cast<float*>(lists + W);
     const int e = blockIdx.x;
     const uint32_t h0 = G.goff[(size_t)e * cells];
     for (int i = tid; i <= cells; i += nt) soff[i] = G.goff[(size_t)e * cells + i] - h0;
@@ -368,7 +522,7 @@ __global__ void __launch_bounds__(kGsThreads) compass_groups_kernel(const FindAr
     const bool search = A.gec == 0 || n <= (uint32_t)A.gec;  // Global Event Cut (Sec. VI)
     const uint32_t t0 = A.trk_off[e], tn = A.trk_off[e + 1] - t0;
     for (uint32_t k = (uint32_t)w; k < tn; k += (uint32_t)W)
-        gs_track(A, G, trk + w, ft, X, soff, sedge, h0, n, e, t0 + k, search, lane);
+        gs_track(A, G, trk + w, lists + w, ft, X, soff, sedge, h0, n, e, t0 + k, search, lane);
 }
 
 }  // namespace utc
@@ -414,7 +568,8 @@ extern "C" int compass_find_groups(ut_ctx* ctx, const ut_group_hits* hits, const
     for (int k = 0; k <= kGsMaxGroups; ++k) G.edges[k] = k <= gg->n_groups ? gg->edges[k] : 0.f;
     const int NG = gg->n_groups, W = kGsThreads / 32;
     const size_t smem = (((size_t)(4 * NG + 1) * 4 + 15) & ~(size_t)15) + (((size_t)(NG + 1) * 4 + 15) & ~(size_t)15) +
-                        sizeof(FitTable) + (size_t)W * sizeof(GsTrack) + (size_t)kGsXCap * sizeof(float);
+                        sizeof(FitTable) + (size_t)W * (sizeof(GsTrack) + sizeof(GsList)) +
+                        (size_t)kGsXCap * sizeof(float);
     if (cudaFuncSetAttribute(compass_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return UT_ERR_CUDA;
