@@ -147,3 +147,11 @@ def test_group_search_refused_arguments(g):
         g.compass_find_groups(ctx, gh, b.geom, velo, b.n_events, synth.CompassParams(n_sectors=6), out, 5.0)
     ctx.check(what="refused")
     ctx.close()
+
+
+def test_group_search_dense_layers_walk_the_y_windows(g):
+    """Dense events without a y cut: layers with more candidates than the
+    per-warp list holds (64) take the walking form; same results."""
+    b = generate_grouped(6, tracks=40, hits=6000, seed=62)
+    compare(g, b, synth.CompassParams(), 1e6, min_found=50)
+    compare(g, b, synth.CompassParams(n_candidates=3), 1e6, min_found=50)
