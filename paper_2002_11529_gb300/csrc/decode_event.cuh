@@ -298,15 +298,66 @@ __device__ __forceinline__ DecodedHit decoded_hit(const DecodeArgs& a, int b, ui
     return h;
 }
 
+// Bitonic sorting network on N keys held in registers (N a power of two;
+// every index is a compile-time constant, so nothing leaves the registers).
+template <int N>
+__device__ __forceinline__ void sort_network(uint32_t (&k)[N]) {
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = k[i], y = k[l];
+                    const uint32_t lo = min(x, y), hi = max(x, y);
+                    const bool up = (i & kk) == 0;
+                    k[i] = up ? lo : hi;
+                    k[l] = up ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+// A bank of n <= N hits sorted by one thread: keys (half-strip << 6 | word
+// index, unique, so the order is the stable one) sorted in registers, then
+// the word position of each output slot written to srcm and the bank to
+// bmap.
+template <int N>
+__device__ __forceinline__ void sort_small_bank(const uint16_t* w16, uint32_t wpos0, uint32_t n, int b, uint32_t j0,
+                                                uint16_t* bmap, uint16_t* srcm) {
+    uint32_t k[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        k[i] = (uint32_t)i < n ? ((min(half_strip(w16[i]), (uint32_t)(kKeyBins - 1)) << 6) | (uint32_t)i) : 0xFFFFFFFFu;
+    sort_network<N>(k);
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        if ((uint32_t)r < n) {
+            srcm[j0 + r] = (uint16_t)(wpos0 + (k[r] & 63u));
+            bmap[j0 + r] = (uint16_t)b;
+        }
+    }
+}
+
+// Banks of at most this many hits are sorted by their own thread (sorting
+// network); larger ones up to kSmallBank by a rank per hit.
+constexpr int kNetBank = 16;
+
 // Shared-memory maps of an event of at most map_cap hits, built before its
-// global base is known.  bmap[i] = bank of event-local hit i (filled by one
-// thread per bank).  SORT (B <= 1024): key[i] = (half-strip << 6) | word
-// index for banks of at most kSmallBank hits; the stable rank r of such a
-// hit is the number of keys of its bank below its own, kept in bits 10-15
-// of bmap[i].  Then srcmap[off[b] + r] = position of the hit's word in the
-// event's 16-bit words.  The key array occupies srcmap until the ranks are
-// taken.  Larger banks (any_big: the event has some) are ranked by
-// rank_big_banks straight into srcmap.
+// global base is known.  bmap[i] = bank of output position i.  SORT
+// (B <= 1024): srcmap[i] = position, in the event's 16-bit words, of the
+// word at output position i.  One thread per bank: a bank of at most
+// kNetBank hits is sorted at once by a sorting network in registers.  A
+// bank of up to kSmallBank hits gets, at each of its positions, the key
+// (half-strip << 6) | word index; the stable rank r of a hit is the number
+// of keys of its bank below its own (counted per hit, kept in bits 10-15 of
+// bmap), then srcmap[off[b] + r] = its word position (the keys occupy
+// srcmap until the ranks are taken).  Larger banks (any_big: the event has
+// some) are ranked by rank_big_banks straight into srcmap.  The rank and
+// inverse passes run only when the event has such banks.
 template <bool SORT>
 __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total,
                           bool any_big, uint64_t nw) {
@@ -318,54 +369,72 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
     auto key_of = [](uint32_t w, uint32_t k) {
         return (uint16_t)((min(half_strip(w), (uint32_t)(kKeyBins - 1)) << 6) | k);
     };
+    bool ranked = false;  // a bank above kNetBank and up to kSmallBank hits
     for (int b = tid; b < B; b += nt) {
         const uint32_t j0 = off[b], n = off[b + 1] - j0;
         if (!chk(j0 + n <= a.map_cap, a.status, 104)) continue;
         if (SORT && n <= (uint32_t)kSmallBank) {
             if (!chk((uint64_t)evw[b] + 1 + (n + 1) / 2 <= nw, a.status, 110)) continue;
-            const uint32_t* w32 = evw + evw[b] + 1;  // two words per u32, low half first
-            for (uint32_t k = 0; k < n; k += 2) {
-                const uint32_t v = w32[k >> 1];
-                bmap[j0 + k] = (uint16_t)b;
-                srcm[j0 + k] = key_of(v & 0xFFFFu, k);
-                if (k + 1 < n) {
-                    bmap[j0 + k + 1] = (uint16_t)b;
-                    srcm[j0 + k + 1] = key_of(v >> 16, k + 1);
+            const uint32_t wpos0 = 2u * (evw[b] + 1u);
+            const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw) + wpos0;
+            if (n <= 4) {
+                sort_small_bank<4>(w16, wpos0, n, b, j0, bmap, srcm);
+            } else if (n <= 8) {
+                sort_small_bank<8>(w16, wpos0, n, b, j0, bmap, srcm);
+            } else if (n <= (uint32_t)kNetBank) {
+                sort_small_bank<kNetBank>(w16, wpos0, n, b, j0, bmap, srcm);
+            } else {
+                ranked = true;
+                const uint32_t* w32 = evw + evw[b] + 1;  // two words per u32, low half first
+                for (uint32_t k = 0; k < n; k += 2) {
+                    const uint32_t v = w32[k >> 1];
+                    bmap[j0 + k] = (uint16_t)b;
+                    srcm[j0 + k] = key_of(v & 0xFFFFu, k);
+                    if (k + 1 < n) {
+                        bmap[j0 + k + 1] = (uint16_t)b;
+                        srcm[j0 + k + 1] = key_of(v >> 16, k + 1);
+                    }
                 }
             }
         } else {
             for (uint32_t j = j0; j < j0 + n; ++j) bmap[j] = (uint16_t)b;
         }
     }
-    __syncthreads();
+    const bool any_ranked = __syncthreads_or(ranked) != 0;
     if constexpr (SORT) {
-        for (uint32_t i = tid; i < total; i += nt) {
-            const int b = bmap[i];
-            const uint32_t o0 = off[b], n = off[b + 1] - o0;
-            if (n > (uint32_t)kSmallBank) continue;
-            const uint32_t key = srcm[i];
-            const uint16_t* K = srcm + o0;
-            uint32_t r = 0, j = 0;
-            for (; j + 4 <= n; j += 4)
-                r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
-                     (uint32_t)(K[j + 3] < key);
-            for (; j < n; ++j) r += (uint32_t)(K[j] < key);
-            bmap[i] = (uint16_t)(b | (r << 10));
+        if (!any_ranked && !any_big) return;
+        auto ranked_bank = [](uint32_t n) { return n > (uint32_t)kNetBank && n <= (uint32_t)kSmallBank; };
+        if (any_ranked) {
+            for (uint32_t i = tid; i < total; i += nt) {
+                const int b = bmap[i];
+                const uint32_t o0 = off[b], n = off[b + 1] - o0;
+                if (!ranked_bank(n)) continue;
+                const uint32_t key = srcm[i];
+                const uint16_t* K = srcm + o0;
+                uint32_t r = 0, j = 0;
+                for (; j + 4 <= n; j += 4)
+                    r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
+                         (uint32_t)(K[j + 3] < key);
+                for (; j < n; ++j) r += (uint32_t)(K[j] < key);
+                bmap[i] = (uint16_t)(b | (r << 10));
+            }
         }
         if (any_big)
             rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
                 srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
             });
         __syncthreads();
-        for (uint32_t i = tid; i < total; i += nt) {
-            const uint32_t v = bmap[i];
-            const int b = (int)(v & 0x3FFu);
-            const uint32_t o0 = off[b];
-            if (off[b + 1] - o0 > (uint32_t)kSmallBank) continue;
-            if (!chk(o0 + (v >> 10) < a.map_cap, a.status, 105)) continue;
-            srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
+        if (any_ranked) {
+            for (uint32_t i = tid; i < total; i += nt) {
+                const uint32_t v = bmap[i];
+                const int b = (int)(v & 0x3FFu);
+                const uint32_t o0 = off[b];
+                if (!ranked_bank(off[b + 1] - o0)) continue;
+                if (!chk(o0 + (v >> 10) < a.map_cap, a.status, 105)) continue;
+                srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
