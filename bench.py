@@ -62,6 +62,9 @@ def parse():
                     help="skip the uneven-workload form comparison, serving and alignment measurements")
     ap.add_argument("--physics", action="store_true",
                     help="also run the sectors x candidates physics sweep and the kick-map workload")
+    ap.add_argument("--only", default=None,
+                    choices=["sector_groups", "alignment", "uneven_workload", "serving"],
+                    help="run only this variant measurement and print its detail line (profiling)")
     return ap.parse_args()
 
 
@@ -697,8 +700,15 @@ def main():
         dist.init_process_group("nccl")
     g.build.build()
 
-    batch = make_batch(args.workload, rank, args.events)
     params = synth.CompassParams()
+    if args.only is not None:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        fn = {"sector_groups": lambda: measure_sector_groups(g), "alignment": lambda: measure_alignment(g, params),
+              "uneven_workload": lambda: time_forms_on_uneven_workload(g, params, flush),
+              "serving": lambda: measure_serving(g, params)}[args.only]
+        print(f"detail {args.only} {json.dumps(fn())}", flush=True)
+        return
+    batch = make_batch(args.workload, rank, args.events)
     ctx = g.Context(batch.geom)
     pipe = g.Pipeline(ctx, batch, params)
     stream = torch.cuda.current_stream()

@@ -376,25 +376,44 @@ __device__ void gs_track(const FindArgs& A, const GroupSearchArgs& G, GsTrack* T
     }
     if (!search || (A.vflags[t] & 1u)) return;
     // extrapolation (lane l = layer l), y at the plane, group holding u
-    double u = 0.0;
     float hi = 0.f, lo = 0.f, y = 0.f;
     int c = 0;
     const int NG = G.NG;
     if (lane < 4) {
         predict_pair(A, vx, vy, vtx, vty, lane, hi, lo);
-        u = (double)hi + (double)lo;
         const double dz = (double)A.z[lane] - (double)A.z_velo;
         y = (float)((double)vy + (double)vty * dz);
-        // c = number of interior edges k in [1, NG - 1] with edges[k] <= u
+        // c = number of interior edges k in [1, NG - 1] with edges[k] <= u,
+        // u = hi + lo in double.  For a float edge e != hi and a pair with
+        // |lo| below half of hi's last place, e <= u exactly when e < hi (the
+        // neighbouring floats of hi lie at least half a last place away); a
+        // search that meets e == hi, or a pair with a larger lo, decides in
+        // double instead
+        const float half_ulp = 0.5f * __int_as_float(__float_as_int(fabsf(hi)) & 0x7F800000) * 1.1920929e-7f;
+        const bool norm = fabsf(lo) < half_ulp || lo == 0.f;
+        bool tie = !norm;
         int a = 1, b = NG;
-        while (a < b) {
+        while (a < b && !tie) {
             const int m = (a + b) >> 1;
-            if ((double)sedge[m] <= u) a = m + 1; else b = m;
+            const float e = sedge[m];
+            tie = e == hi;
+            if (e < hi) a = m + 1; else b = m;
+        }
+        if (tie) {
+            const double u = (double)hi + (double)lo;
+            a = 1;
+            b = NG;
+            while (a < b) {
+                const int m = (a + b) >> 1;
+                if ((double)sedge[m] <= u) a = m + 1; else b = m;
+            }
         }
         c = a - 1;
     }
-    const double u0 = __shfl_sync(0xffffffffu, u, 0);
-    if (!(u0 >= (double)A.x_min && u0 <= A.x_max)) return;  // acceptance (Sec. V-A)
+    // acceptance (Sec. V-A) on u_0 = hi + lo in double
+    const float hi0 = __shfl_sync(0xffffffffu, hi, 0), lo0 = __shfl_sync(0xffffffffu, lo, 0);
+    const double u0 = (double)hi0 + (double)lo0;
+    if (!(u0 >= (double)A.x_min && u0 <= A.x_max)) return;
     float kqt = 0.f, kick = A.kick_k;
     if (A.kmap) {
         kick = kick_at(A, vtx, vty);
