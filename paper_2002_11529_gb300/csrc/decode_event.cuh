@@ -438,19 +438,35 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
     }
 }
 
-// Writes of a mapped event in output order; groups of four outputs that
-// start on a 16-byte boundary in global memory use vector stores.
+// Writes of an event in output order; groups of four outputs that start on
+// a 16-byte boundary in global memory use vector stores.  SORT: the bank and
+// the source word of each output position come from the shared-memory maps.
+// Bank order: output position o is word o - off[b] of the bank b holding it,
+// read from the bank map when the event has one (from_map), else found by a
+// binary search over the event-local offsets for the first output of a
+// group and by a forward walk for the others.
 template <bool SORT>
 __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, const uint32_t* evw,
                              unsigned long long base, uint32_t total, bool fits, float* sx, uint32_t sx_cap,
-                             uint64_t nw) {
+                             uint64_t nw, bool from_map) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int B = 4 * a.S;
     const uint32_t* off = sm.off;
     const uint16_t* bmap = sm.bmap;
     const uint16_t* srcm = sm.srcmap;
-    auto hit_at = [&](uint32_t o) -> DecodedHit {
-        const int b = SORT ? (int)(ld_chk(bmap, o, a.map_cap, a.status, 107) & 0x3FFu)
-                           : (int)ld_chk(bmap, o, a.map_cap, a.status, 107);
+    // bank of output position o: from the map (SORT) or from the offsets,
+    // starting at bank `hint` (a bank at or before it)
+    auto bank_of = [&](uint32_t o, int hint) -> int {
+        if constexpr (SORT) {
+            return (int)(ld_chk(bmap, o, a.map_cap, a.status, 107) & 0x3FFu);
+        } else {
+            if (from_map) return (int)ld_chk(bmap, o, a.map_cap, a.status, 107);
+            int b = hint;
+            while (off[b + 1] <= o) ++b;
+            return b;
+        }
+    };
+    auto hit_at = [&](uint32_t o, int b) -> DecodedHit {
         const long long wpos = SORT ? (long long)ld_chk(srcm, o, a.map_cap, a.status, 107)
                                     : 2ll * ((long long)evw[b] + 1) + (long long)(o - off[b]);
         const uint32_t w = (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(evw), wpos, 2ll * (long long)nw,
@@ -459,7 +475,8 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
         return decoded_hit(a, b, w);
     };
     auto one = [&](uint32_t o) {
-        const DecodedHit h = hit_at(o);
+        const int b = bank_of(o, SORT || from_map ? 0 : find_bank(off, B, o));
+        const DecodedHit h = hit_at(o, b);
         if (sx != nullptr && o < sx_cap) sx[o] = h.x;
         if (!fits) return;
         const size_t g = (size_t)(base + o);
@@ -477,9 +494,11 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
     for (uint32_t q = tid; q < nq; q += nt) {
         const uint32_t o = head + 4 * q;
         DecodedHit h[4];
+        int b = SORT || from_map ? 0 : find_bank(off, B, o);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            h[j] = hit_at(o + j);
+            b = bank_of(o + j, b);
+            h[j] = hit_at(o + j, b);
             if (sx != nullptr && o + j < sx_cap) sx[o + j] = h[j].x;
         }
         if (!fits) continue;
@@ -583,9 +602,12 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     // time to publish theirs.
     if (tid == 0)
         st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
-    // (sorted: bank and rank share 16 bits, word positions fit 16 bits)
-    const bool mapped = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
-    if (mapped) map_event<SORT>(a, sm, evw, total, any_big, nw);
+    // Events of at most map_cap hits build the shared-memory maps (sorted:
+    // bank and rank share 16 bits, word positions fit 16 bits); larger
+    // bank-order events are written in output order without them.
+    const bool from_map = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
+    const bool mapped = SORT ? from_map : ev_ok;
+    if (from_map) map_event<SORT>(a, sm, evw, total, any_big, nw);
     if (tid < 32) {
         const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status, a.spin_limit) : 0ull;
         if (tid == 0) {
@@ -608,7 +630,7 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     // Decode.  Mapped events are written in output order; larger ones use
     // one thread per hit (bank by binary search) writing at its ranked slot.
     if (mapped) {
-        write_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap, nw);
+        write_mapped<SORT>(a, e, sm, evw, base, total, fits, sx, sx_cap, nw, from_map);
         return;
     }
     for (uint32_t i = tid; i < total; i += nt) {
