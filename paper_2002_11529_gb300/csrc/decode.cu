@@ -217,8 +217,8 @@ extern "C" int ut_decode(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw_word
     a.ticket = static_cast<unsigned int*>(d_workspace);
     a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     a.status = ctx->d_status;
-    a.stage_words = kStageWordsDefault;
-    a.map_cap = B <= 65536 ? kMapCapDefault : 0;
+    a.stage_words = sorted ? kStageWordsDefault : kStageWordsBank;
+    a.map_cap = B <= 65536 ? (sorted ? kMapCapDefault : kMapCapBank) : 0;
     a.vec_ok = hits_aligned16(out);
     a.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;
@@ -345,8 +345,8 @@ extern "C" int ut_decode_noalloc(const ut_geometry* geom, const uint32_t* d_raw,
     a.ticket = static_cast<unsigned int*>(scratch);
     a.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 16);
     a.status = d_status;
-    a.stage_words = kStageWordsDefault;
-    a.map_cap = B <= 65536 ? kMapCapDefault : 0;
+    a.stage_words = sorted ? kStageWordsDefault : kStageWordsBank;
+    a.map_cap = B <= 65536 ? (sorted ? kMapCapDefault : kMapCapBank) : 0;
     a.vec_ok = hits_aligned16(out);
     a.spin_limit = kSpinLimit;
     // the array keeps the previous call's contents: clear the counter and the

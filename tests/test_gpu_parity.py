@@ -111,6 +111,20 @@ def test_decode_event_larger_than_stage(g):
         assert_hits_equal(g.hits_to_numpy(hb), orc, orc.n)
 
 
+@pytest.mark.parametrize("hits", [3000, 4500, 9000, 13000])
+def test_decode_event_sizes_around_the_map_and_stage_limits(g, hits):
+    """Events below and above the bank map's capacity (bank order: a map up
+    to 4096 hits, the map-free output-order path above it) and below and
+    above the staged size, in both output orders."""
+    b = synth.generate(n_events=5, n_sectors=256, tracks=100, hits=hits, seed=31 + hits)
+    ctx = ctx_for(g, b.geom)
+    for sorted_ in (False, True):
+        code, _, hb = run_decode(g, ctx, b.raw, b.ev_off, b.n_events, b.geom, sorted_)
+        assert code == 0
+        rc, orc, _ = oracle.decode(b.raw, b.ev_off, b.n_events, b.geom, sorted_)
+        assert_hits_equal(g.hits_to_numpy(hb), orc, orc.n)
+
+
 def test_decode_empty_batch(g):
     geom = synth.Geometry(n_sectors=4)
     ctx = ctx_for(g, geom)
