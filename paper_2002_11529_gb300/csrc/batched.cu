@@ -243,7 +243,7 @@ extern "C" int ut_run_batched(ut_ctx* ctx, const uint32_t* d_raw, uint64_t n_raw
     D.tile_state = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_workspace) + 16);
     D.status = ctx->d_status;
     D.stage_words = (uint32_t)stage_words;
-    D.map_cap = 4 * S <= 1024 ? kMapCapDefault : 0;  // sorted bank-map path (bank and rank share 16 bits)
+    D.map_cap = 4 * S <= 65536 ? kMapCapDefault : 0;  // sorted bank-map path (banks in 16 bits)
     D.vec_ok = hits_aligned16(hits_out);
     D.spin_limit = ctx->wait_limit;
     if (cudaMemsetAsync(d_workspace, 0, ut_decode_workspace_size(n_events), st) != cudaSuccess) return UT_ERR_CUDA;

@@ -349,98 +349,120 @@ __device__ __forceinline__ void sort_small_bank(const uint16_t* w16, uint32_t wp
 }
 
 // Banks of at most this many hits are sorted by their own thread (sorting
-// network); larger ones up to kSmallBank by a rank per hit.
+// network of 8 or 16 keys); larger ones up to kSmallBank by the whole warp
+// that meets them.
 constexpr int kNetBank = 16;
+
+// Sorts one bank of kNetBank < n <= kSmallBank hits with the L lanes of a
+// warp (mask wmask, lanes 0..L-1): the keys (half-strip << 6) | word index
+// are written to the bank's own range of srcm, each lane counts the keys
+// below those of its words (rank; the keys are unique, so the order is the
+// stable one), and after the warp has read every key the word position of
+// each hit is stored at its rank.
+__device__ __forceinline__ void warp_sort_bank(const uint16_t* w16, uint32_t wpos0, uint32_t n, int b, uint32_t j0,
+                                               uint16_t* bmap, uint16_t* srcm, int lane, int L, uint32_t wmask) {
+    uint16_t* K = srcm + j0;
+    for (uint32_t j = (uint32_t)lane; j < n; j += (uint32_t)L) {
+        K[j] = (uint16_t)((min(half_strip(w16[j]), (uint32_t)(kKeyBins - 1)) << 6) | j);
+        bmap[j0 + j] = (uint16_t)b;
+    }
+    __syncwarp(wmask);
+    if (n <= (uint32_t)L) {  // one word per lane
+        const uint32_t j = (uint32_t)lane;
+        const uint32_t key = j < n ? (uint32_t)K[j] : 0u;
+        uint32_t r = 0;
+        for (uint32_t i = 0; i < n; ++i) r += (uint32_t)((uint32_t)K[i] < key);
+        __syncwarp(wmask);
+        if (j < n) K[r] = (uint16_t)(wpos0 + j);
+        __syncwarp(wmask);
+        return;
+    }
+    // three words per lane in each round
+    for (uint32_t jb = 0; jb < n; jb += 3u * (uint32_t)L) {
+        uint32_t key[3], r[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const uint32_t j = jb + (uint32_t)lane + (uint32_t)(m * L);
+            key[m] = j < n ? (uint32_t)K[j] : 0u;
+        }
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t ki = K[i];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) r[m] += (uint32_t)(ki < key[m]);
+        }
+        __syncwarp(wmask);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const uint32_t j = jb + (uint32_t)lane + (uint32_t)(m * L);
+            if (j < n) K[r[m]] = (uint16_t)(wpos0 + j);
+        }
+        __syncwarp(wmask);
+    }
+}
 
 // Shared-memory maps of an event of at most map_cap hits, built before its
 // global base is known.  bmap[i] = bank of output position i.  SORT
 // (B <= 1024): srcmap[i] = position, in the event's 16-bit words, of the
 // word at output position i.  One thread per bank: a bank of at most
-// kNetBank hits is sorted at once by a sorting network in registers.  A
-// bank of up to kSmallBank hits gets, at each of its positions, the key
-// (half-strip << 6) | word index; the stable rank r of a hit is the number
-// of keys of its bank below its own (counted per hit, kept in bits 10-15 of
-// bmap), then srcmap[off[b] + r] = its word position (the keys occupy
-// srcmap until the ranks are taken).  Larger banks (any_big: the event has
-// some) are ranked by rank_big_banks straight into srcmap.  The rank and
-// inverse passes run only when the event has such banks.
+// kNetBank hits is sorted at once by a sorting network in registers; the
+// warp then sorts together, one after the other, its banks of up to
+// kSmallBank hits (warp_sort_bank).  Larger banks (any_big: the event has
+// some) are ranked by rank_big_banks straight into srcmap.  The maps are
+// complete after the next __syncthreads of the caller.
 template <bool SORT>
-__device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, uint32_t total,
-                          bool any_big, uint64_t nw) {
+__device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, bool any_big,
+                          uint64_t nw) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int B = 4 * a.S;
     const uint32_t* off = sm.off;
     uint16_t* bmap = sm.bmap;
     uint16_t* srcm = sm.srcmap;
-    auto key_of = [](uint32_t w, uint32_t k) {
-        return (uint16_t)((min(half_strip(w), (uint32_t)(kKeyBins - 1)) << 6) | k);
-    };
-    bool ranked = false;  // a bank above kNetBank and up to kSmallBank hits
-    for (int b = tid; b < B; b += nt) {
-        const uint32_t j0 = off[b], n = off[b + 1] - j0;
-        if (!chk(j0 + n <= a.map_cap, a.status, 104)) continue;
-        if (SORT && n <= (uint32_t)kSmallBank) {
-            if (!chk((uint64_t)evw[b] + 1 + (n + 1) / 2 <= nw, a.status, 110)) continue;
-            const uint32_t wpos0 = 2u * (evw[b] + 1u);
-            const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw) + wpos0;
-            if (n <= 4) {
-                sort_small_bank<4>(w16, wpos0, n, b, j0, bmap, srcm);
-            } else if (n <= 8) {
-                sort_small_bank<8>(w16, wpos0, n, b, j0, bmap, srcm);
-            } else if (n <= (uint32_t)kNetBank) {
-                sort_small_bank<kNetBank>(w16, wpos0, n, b, j0, bmap, srcm);
-            } else {
-                ranked = true;
-                const uint32_t* w32 = evw + evw[b] + 1;  // two words per u32, low half first
-                for (uint32_t k = 0; k < n; k += 2) {
-                    const uint32_t v = w32[k >> 1];
-                    bmap[j0 + k] = (uint16_t)b;
-                    srcm[j0 + k] = key_of(v & 0xFFFFu, k);
-                    if (k + 1 < n) {
-                        bmap[j0 + k + 1] = (uint16_t)b;
-                        srcm[j0 + k + 1] = key_of(v >> 16, k + 1);
+    const int lane = tid & 31, wt0 = tid - lane;
+    const int L = min(32, nt - wt0);  // lanes of this warp
+    const uint32_t wmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+    // the same number of rounds for every lane of a warp (warp-wide sorts)
+    for (int k0 = 0; wt0 + k0 < B; k0 += nt) {
+        const int b = tid + k0;
+        bool coop = false;
+        if (b < B) {
+            const uint32_t j0 = off[b], n = off[b + 1] - j0;
+            if (chk(j0 + n <= a.map_cap, a.status, 104)) {
+                if (SORT && n <= (uint32_t)kSmallBank) {
+                    if (chk((uint64_t)evw[b] + 1 + (n + 1) / 2 <= nw, a.status, 110)) {
+                        if (n <= (uint32_t)kNetBank) {
+                            const uint32_t wpos0 = 2u * (evw[b] + 1u);
+                            const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw) + wpos0;
+                            if (n <= 8)
+                                sort_small_bank<8>(w16, wpos0, n, b, j0, bmap, srcm);
+                            else
+                                sort_small_bank<kNetBank>(w16, wpos0, n, b, j0, bmap, srcm);
+                        } else {
+                            coop = true;
+                        }
                     }
+                } else {
+                    for (uint32_t j = j0; j < j0 + n; ++j) bmap[j] = (uint16_t)b;
                 }
             }
-        } else {
-            for (uint32_t j = j0; j < j0 + n; ++j) bmap[j] = (uint16_t)b;
         }
-    }
-    const bool any_ranked = __syncthreads_or(ranked) != 0;
-    if constexpr (SORT) {
-        if (!any_ranked && !any_big) return;
-        auto ranked_bank = [](uint32_t n) { return n > (uint32_t)kNetBank && n <= (uint32_t)kSmallBank; };
-        if (any_ranked) {
-            for (uint32_t i = tid; i < total; i += nt) {
-                const int b = bmap[i];
-                const uint32_t o0 = off[b], n = off[b + 1] - o0;
-                if (!ranked_bank(n)) continue;
-                const uint32_t key = srcm[i];
-                const uint16_t* K = srcm + o0;
-                uint32_t r = 0, j = 0;
-                for (; j + 4 <= n; j += 4)
-                    r += (uint32_t)(K[j] < key) + (uint32_t)(K[j + 1] < key) + (uint32_t)(K[j + 2] < key) +
-                         (uint32_t)(K[j + 3] < key);
-                for (; j < n; ++j) r += (uint32_t)(K[j] < key);
-                bmap[i] = (uint16_t)(b | (r << 10));
+        if constexpr (SORT) {
+            uint32_t cm = __ballot_sync(wmask, coop);
+            while (cm) {
+                const int src = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const int bb = wt0 + k0 + src;
+                const uint32_t j0 = off[bb], n = off[bb + 1] - j0;
+                const uint32_t wpos0 = 2u * (evw[bb] + 1u);
+                warp_sort_bank(reinterpret_cast<const uint16_t*>(evw) + wpos0, wpos0, n, bb, j0, bmap, srcm, lane, L,
+                               wmask);
             }
         }
+    }
+    if constexpr (SORT) {
         if (any_big)
             rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
                 srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
             });
-        __syncthreads();
-        if (any_ranked) {
-            for (uint32_t i = tid; i < total; i += nt) {
-                const uint32_t v = bmap[i];
-                const int b = (int)(v & 0x3FFu);
-                const uint32_t o0 = off[b];
-                if (!ranked_bank(off[b + 1] - o0)) continue;
-                if (!chk(o0 + (v >> 10) < a.map_cap, a.status, 105)) continue;
-                srcm[o0 + (v >> 10)] = (uint16_t)(2u * (evw[b] + 1u) + (i - o0));
-            }
-            __syncthreads();
-        }
     }
 }
 
@@ -464,7 +486,7 @@ __device__ void write_mapped(const DecodeArgs& a, int e, const DecodeSmem& sm, c
     // starting at bank `hint` (a bank at or before it)
     auto bank_of = [&](uint32_t o, int hint) -> int {
         if constexpr (SORT) {
-            return (int)(ld_chk(bmap, o, a.map_cap, a.status, 107) & 0x3FFu);
+            return (int)ld_chk(bmap, o, a.map_cap, a.status, 107);
         } else {
             if (from_map) return (int)ld_chk(bmap, o, a.map_cap, a.status, 107);
             int b = hint;
@@ -609,11 +631,11 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     if (tid == 0)
         st_volatile_u64(a.tile_state + e, (e == 0 ? kFlagPrefix : kFlagAggregate) | (unsigned long long)total);
     // Events of at most map_cap hits build the shared-memory maps (sorted:
-    // bank and rank share 16 bits, word positions fit 16 bits); larger
-    // bank-order events are written in output order without them.
-    const bool from_map = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || (B <= 1024 && nw < 32768));
+    // word positions fit 16 bits); larger bank-order events are written in
+    // output order without them.
+    const bool from_map = ev_ok && sm.bmap != nullptr && total <= a.map_cap && (!SORT || nw < 32768);
     const bool mapped = SORT ? from_map : ev_ok;
-    if (from_map) map_event<SORT>(a, sm, evw, total, any_big, nw);
+    if (from_map) map_event<SORT>(a, sm, evw, any_big, nw);
     if (tid < 32) {
         const unsigned long long excl = e > 0 ? lookback(a.tile_state, e, a.status, a.spin_limit) : 0ull;
         if (tid == 0) {
