@@ -109,9 +109,73 @@ def workload_config(wl, batch, form, extra=None):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    NVML is read directly (libnvidia-ml through ctypes, read-only queries)
+    from a thread polling about every millisecond, so that a timed region of
+    a few milliseconds still gets samples; nvidia-smi's 100 ms loop is the
+    fallback where NVML cannot be opened."""
+
+    # NVML clocks event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index):
+        import ctypes
+        import threading
+        import torch
+        self.p = None
+        self.samples = []
+        self.stop_flag = threading.Event()
+        self.t = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            h = ctypes.c_void_p()
+            # the CUDA device's own GPU (CUDA_VISIBLE_DEVICES may renumber):
+            # by UUID, else by PCI bus id, else by index
+            props = torch.cuda.get_device_properties(index)
+            uuid = getattr(props, "uuid", None)
+            ok = False
+            if uuid is not None:
+                u = str(uuid)
+                ok = nv.nvmlDeviceGetHandleByUUID((u if u.startswith("GPU-") else "GPU-" + u).encode(),
+                                                  ctypes.byref(h)) == 0
+            if not ok and hasattr(props, "pci_bus_id"):
+                bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                            getattr(props, "pci_device_id", 0))
+                ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+            if not ok and nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                raise OSError("nvmlDeviceGetHandle")
+            self.handle_by = "uuid/pci" if ok else "index"
+            mx = ctypes.c_uint()
+            nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # 1 = NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+            def poll():
+                clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+                while not self.stop_flag.is_set():
+                    if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                        r = rs.value if get_reasons(h, ctypes.byref(rs)) == 0 else 0
+                        self.samples.append((float(clk.value), int(r)))
+                    time.sleep(0.001)
+
+            self.t = threading.Thread(target=poll, daemon=True)
+            self.t.start()
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 2.0:  # sampling before the region starts
+                time.sleep(0.001)
+            self.samples.clear()
+            self.how = "nvml"
+        except Exception:  # no NVML library or device: nvidia-smi
+            self.t = None
+            self._smi(index)
+
+    def _smi(self, index):
+        self.how = "nvidia-smi"
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -124,6 +188,16 @@ class Clocks:
             self.p = None
 
     def stop(self):
+        if self.t is not None:
+            self.stop_flag.set()
+            self.t.join(timeout=2)
+            if not self.samples:
+                return None
+            reasons = set()
+            for _, r in self.samples:
+                reasons |= {n for bit, n in self.REASONS.items() if r & bit}
+            return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(reasons), "samples": len(self.samples), "source": f"nvml ({self.handle_by}), ~1 ms polling"}
         if self.p is None:
             return None
         self.p.terminate()
@@ -151,7 +225,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 100 ms loop"}
 
 
 def peaks():
