@@ -6,10 +6,13 @@
 //
 // One block per event, no waits.  The order is a stable counting sort on
 // the key (layer, group, row): y_begin is a function of the row, so the
-// row orders y_begin, and raw order breaks ties.  Counts per key (shared
-// atomics), an exclusive scan by one warp, then one warp places the hits in
-// raw order, 32 at a time: lanes with equal keys (match-any) take
-// consecutive slots, so the placement is stable and deterministic.
+// row orders y_begin, and raw order breaks ties.  The event's hits are cut
+// into one contiguous chunk per warp; each warp counts the keys of its chunk
+// in its own table (shared atomics), a block scan over the keys gives every
+// key's first slot, each warp's table becomes its start within the key
+// (earlier chunks first), and the warps place their chunks in raw order, 32
+// hits at a time: lanes with equal keys (match-any) take consecutive slots,
+// so the placement is stable and deterministic.
 
 #include <cmath>
 
@@ -21,6 +24,8 @@ namespace utc {
 constexpr int kGroupThreads = 256;
 constexpr int kMaxGroups = 128, kMaxRows = 8;
 constexpr int kMaxKeys = 4 * kMaxGroups * kMaxRows;
+constexpr size_t kGroupSmemMax = 96 * 1024;  // per-warp key tables and totals
+static_assert(2 * kMaxKeys * sizeof(uint32_t) <= kGroupSmemMax, "one warp's table always fits");
 
 struct GroupArgs {
     const uint32_t* id;
@@ -42,37 +47,114 @@ struct GroupArgs {
     unsigned long long* status;
 };
 
-// Key (layer, group, row) of a hit and its x at y = 0; -1 for an id that
-// names no sensor of the geometry (not from the bank-order decode).
-__device__ __forceinline__ int group_key(const GroupArgs& a, const float* edges, uint32_t id, float& x, int& l,
-                                         int& r) {
-    l = (int)(id >> 24);
-    const int s = (int)((id >> 16) & 0xFFu);
-    if (l > 3 || s >= a.B / 4) return -1;
-    const uint32_t wd = id & 0xFFFFu;
-    const int c = s / a.rows;
-    r = s - c * a.rows;
-    const uint32_t h = 2u * (wd & 0x3FFu) + ((wd >> 10) & 1u);
+// Per-block lookup tables: column and row of each sector, and the range of
+// groups a column's strips can fall in (kMaxSectors = 256 sectors per layer).
+constexpr int kMaxSectors = 256;
+struct GroupTables {
+    uint8_t col[kMaxSectors], row[kMaxSectors], glo[kMaxSectors], ghi[kMaxSectors];
+};
+
+// x at y = 0 of half-strip h of column c.
+__device__ __forceinline__ float group_x(const GroupArgs& a, int c, uint32_t h) {
     const float x0 = (float)c * a.sector_pitch + a.x_min;
     const float d = ((float)h + 0.5f) * a.hp;
-    x = x0 + d;
-    // group: the largest k in [0, n_groups - 1] with k == 0 or edges[k] <= x
-    int lo = 0, hi = a.n_groups - 1;
+    return x0 + d;
+}
+
+// The largest k in [lo, hi] with k == lo or edges[k] <= x (edges increasing).
+__device__ __forceinline__ int group_in(const float* edges, float x, int lo, int hi) {
     while (lo < hi) {
         const int m = (lo + hi + 1) >> 1;
         if (edges[m] <= x) lo = m; else hi = m - 1;
     }
-    return (l * a.n_groups + lo) * a.rows + r;
+    return lo;
 }
 
-__global__ void __launch_bounds__(kGroupThreads) sector_groups_kernel(const GroupArgs a) {
-    __shared__ uint32_t cnt[kMaxKeys];
+// Fills the tables (then the caller synchronises).  x is non-decreasing in
+// the half-strip (rounded products and sums of non-negative steps), so the
+// group of any strip of column c lies between those of its first and last
+// half-strips, and the search inside that range gives the full search's
+// group: the largest k in [0, n_groups - 1] with k == 0 or edges[k] <= x.
+__device__ void group_tables(const GroupArgs& a, const float* edges, GroupTables* t) {
+    const int S = a.B / 4;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const int c = s / a.rows;
+        t->col[s] = (uint8_t)c;
+        t->row[s] = (uint8_t)(s - c * a.rows);
+    }
+    for (int c = threadIdx.x; c < S / a.rows; c += blockDim.x) {
+        t->glo[c] = (uint8_t)group_in(edges, group_x(a, c, 0u), 0, a.n_groups - 1);
+        t->ghi[c] = (uint8_t)group_in(edges, group_x(a, c, 2047u), 0, a.n_groups - 1);
+    }
+}
+
+// Key (layer, group, row) of a hit and its x at y = 0; -1 for an id that
+// names no sensor of the geometry (not from the bank-order decode).
+__device__ __forceinline__ int group_key(const GroupArgs& a, const float* edges, const GroupTables* t, uint32_t id,
+                                         float& x, int& l, int& r) {
+    l = (int)(id >> 24);
+    const int s = (int)((id >> 16) & 0xFFu);
+    if (l > 3 || s >= a.B / 4) return -1;
+    const uint32_t wd = id & 0xFFFFu;
+    const int c = t->col[s];
+    r = t->row[s];
+    const uint32_t h = 2u * (wd & 0x3FFu) + ((wd >> 10) & 1u);
+    x = group_x(a, c, h);
+    const int g = group_in(edges, x, t->glo[c], t->ghi[c]);
+    return (l * a.n_groups + g) * a.rows + r;
+}
+
+// Exclusive scan of v[0, n) in place by the whole block; returns the total.
+__device__ uint32_t block_scan_excl(uint32_t* v, int n, uint32_t* warp_tot) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    const int per = (n + nt - 1) / nt;
+    const int k0 = min(tid * per, n), k1 = min(k0 + per, n);
+    uint32_t local = 0;
+    for (int k = k0; k < k1; ++k) local += v[k];
+    uint32_t incl = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += t;
+        }
+        if (lane < nw) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = (incl - local) + (wid > 0 ? warp_tot[wid - 1] : 0u);
+    const uint32_t total = warp_tot[nw - 1];
+    for (int k = k0; k < k1; ++k) {
+        const uint32_t c = v[k];
+        v[k] = run;
+        run += c;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Dynamic shared memory: W per-warp key tables and the key totals.
+__global__ void __launch_bounds__(kGroupThreads) sector_groups_kernel(const GroupArgs a, int W) {
+    extern __shared__ uint32_t gsm[];
     __shared__ float edges[kMaxGroups + 1];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    __shared__ uint32_t warp_tot[kGroupThreads / 32];
+    __shared__ GroupTables tabs;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int e = blockIdx.x;
     const int K = 4 * a.n_groups * a.rows;
-    for (int i = tid; i < K; i += nt) cnt[i] = 0u;
+    uint32_t* cw = gsm;                   // W x K: per-warp counts, then starts
+    uint32_t* tot = gsm + (size_t)W * K;  // K: totals, then first slots
+    for (int i = tid; i < W * K; i += nt) cw[i] = 0u;
     for (int i = tid; i <= a.n_groups; i += nt) edges[i] = a.edges[i];
+    __syncthreads();
+    group_tables(a, edges, &tabs);
     __syncthreads();
     const uint32_t h0 = a.hit_off[(size_t)e * a.B], h1 = a.hit_off[(size_t)(e + 1) * a.B];
     if (h1 < h0 || h1 > a.capacity || h1 > a.in_capacity) {  // the same for every thread of the block
@@ -80,57 +162,72 @@ __global__ void __launch_bounds__(kGroupThreads) sector_groups_kernel(const Grou
         return;
     }
     const uint32_t n = h1 - h0;
-    for (uint32_t i = tid; i < n; i += nt) {
-        float x;
-        int l, r;
-        const int key = group_key(a, edges, a.id[h0 + i], x, l, r);
-        if (key >= 0) atomicAdd(&cnt[key], 1u);
-        else report(a.status, UT_ERR_ARG, e, -1);
+    // chunk of warp w: [w ch, (w + 1) ch) of the event's hits
+    const uint32_t ch = (n + (uint32_t)W - 1) / (uint32_t)W;
+    const uint32_t c0 = min(n, (uint32_t)wid * ch), c1 = min(n, c0 + ch);
+    if (wid < W) {
+        uint32_t* mine = cw + (size_t)wid * K;
+        // four independent loads in flight per lane
+        for (uint32_t i0 = c0 + (uint32_t)lane; i0 < c1; i0 += 128) {
+            uint32_t ids[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t i = i0 + 32u * (uint32_t)u;
+                ids[u] = i < c1 ? __ldg(a.id + h0 + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i0 + 32u * (uint32_t)u >= c1) break;
+                float x;
+                int l, r;
+                const int key = group_key(a, edges, &tabs, ids[u], x, l, r);
+                if (key >= 0) atomicAdd(&mine[key], 1u);
+                else report(a.status, UT_ERR_ARG, e, -1);
+            }
+        }
     }
     __syncthreads();
-    // exclusive scan of the K counts by warp 0: lane q takes a contiguous chunk
-    if (tid < 32) {
-        const int chunk = (K + 31) / 32, k0 = min(K, lane * chunk), k1 = min(K, k0 + chunk);
-        uint32_t sum = 0;
-        for (int k = k0; k < k1; ++k) sum += cnt[k];
-        uint32_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        uint32_t run = incl - sum;
-        for (int k = k0; k < k1; ++k) {
-            const uint32_t c = cnt[k];
-            cnt[k] = run;
+    for (int k = tid; k < K; k += nt) {
+        uint32_t t = 0;
+        for (int w = 0; w < W; ++w) t += cw[(size_t)w * K + k];
+        tot[k] = t;
+    }
+    __syncthreads();
+    block_scan_excl(tot, K, warp_tot);
+    for (int k = tid; k < K; k += nt) {
+        uint32_t run = tot[k];
+        for (int w = 0; w < W; ++w) {
+            const uint32_t c = cw[(size_t)w * K + k];
+            cw[(size_t)w * K + k] = run;
             run += c;
         }
     }
-    __syncthreads();
     const int cells = 4 * a.n_groups;
-    for (int k = tid; k < cells; k += nt) a.group_off[(size_t)e * cells + k] = h0 + cnt[k * a.rows];
+    for (int k = tid; k < cells; k += nt) a.group_off[(size_t)e * cells + k] = h0 + tot[k * a.rows];
     if (e == a.n_events - 1 && tid == 0) a.group_off[(size_t)a.n_events * cells] = h1;
     __syncthreads();
-    // stable placement in raw order by warp 0
-    if (tid >= 32) return;
-    for (uint32_t base = 0; base < n; base += 32) {
+    // stable placement of each chunk in raw order by its warp
+    if (wid >= W) return;
+    uint32_t* start = cw + (size_t)wid * K;
+    uint32_t next = c0 + (uint32_t)lane < c1 ? __ldg(a.id + h0 + c0 + lane) : 0u;
+    for (uint32_t base = c0; base < c1; base += 32) {
         const uint32_t i = base + (uint32_t)lane;
-        const bool valid = i < n;
+        const bool valid = i < c1;
         float x = 0.f;
         int l = 0, r = 0, key = K + lane;  // lanes past the end: a key of their own
-        uint32_t id = 0;
+        const uint32_t id = next;  // loaded one round ahead
+        next = i + 32u < c1 ? __ldg(a.id + h0 + i + 32u) : 0u;
         bool use = false;
         if (valid) {
-            id = a.id[h0 + i];
-            const int k = group_key(a, edges, id, x, l, r);
+            const int k = group_key(a, edges, &tabs, id, x, l, r);
             use = k >= 0;
             if (use) key = k;
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-        const uint32_t pos = use ? cnt[key] + rank : 0u;
+        const uint32_t pos = use ? start[key] + rank : 0u;
         __syncwarp();
-        if (use && rank == 0) cnt[key] += (uint32_t)__popc(peers);
+        if (use && rank == 0) start[key] += (uint32_t)__popc(peers);
         __syncwarp();
         if (use) {
             const size_t o = (size_t)h0 + pos;
@@ -188,6 +285,13 @@ extern "C" int ut_sector_groups(ut_ctx* ctx, const ut_hits* in, int n_events, co
     a.group_off = out->group_off;
     a.capacity = out->capacity;
     a.status = ctx->d_status;
-    sector_groups_kernel<<<n_events, kGroupThreads, 0, st>>>(a);
+    // as many warps with their own key table as the shared memory holds
+    const int K = 4 * gg->n_groups * gg->rows;
+    int W = kGroupThreads / 32;
+    while (W > 1 && (size_t)(W + 1) * K * sizeof(uint32_t) > kGroupSmemMax) --W;
+    const size_t smem = (size_t)(W + 1) * K * sizeof(uint32_t);
+    cudaError_t err = cudaFuncSetAttribute(sector_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return UT_ERR_CUDA;
+    sector_groups_kernel<<<n_events, kGroupThreads, smem, st>>>(a, W);
     return check_cuda(cudaGetLastError());
 }

@@ -24,6 +24,9 @@ CASES = {
     "one_row": dict(n_events=8, rows=1, n_groups=6, seed=4),
     "busy": dict(n_events=200, tracks=150, hits=3000, seed=9),
     "max_groups": dict(n_events=6, n_columns=32, rows=7, n_groups=128, tracks=100, hits=2500, seed=10),
+    # 4 x 128 x 8 keys: the most the layout takes (fewer warp tables fit)
+    "max_keys": dict(n_events=5, n_columns=31, rows=8, n_groups=128, tracks=100, hits=3000, seed=12),
+    "one_event_dense": dict(n_events=1, tracks=200, hits=6000, seed=13),
 }
 
 
