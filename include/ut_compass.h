@@ -323,7 +323,8 @@ typedef struct ut_tracks_compact {
 } ut_tracks_compact;
 
 /* Bytes of device scratch that ut_consolidate needs for n_events (a work
- * counter and the per-event look-back state): 16 + 8 * n_events. */
+ * counter and the look-back state of at most n_events parts):
+ * 16 + 8 * n_events. */
 size_t ut_consolidate_workspace_size(int n_events);
 
 /*
@@ -333,7 +334,8 @@ size_t ut_consolidate_workspace_size(int n_events);
  * ut_run_batched wrote (found, hit, qop, chi2, x, tx, nhits are read).
  * Writes the found tracks, in order, to out (rows [0, N)) and
  * d_out_off[e] = first row of event e, d_out_off[n_events] = N.  One
- * single-pass kernel (one block per event, decoupled look-back).
+ * single-pass kernel (one block per contiguous part of the events, at most
+ * one part per SM, decoupled look-back over the parts).
  * Workspace: >= ut_consolidate_workspace_size(n_events) bytes, 16-byte
  * aligned; cleared on `stream` before use.  N > out->capacity records
  * UT_ERR_CAPACITY in the status word (rows past the capacity are not

@@ -53,6 +53,30 @@ def test_consolidation_matches_the_oracle(g):
     assert np.array_equal(tracks["hit"], orc.hit)
 
 
+def test_parts_of_many_events_with_empty_events(g):
+    """2000 events (several events per block part), a third of them with
+    their found flags cleared, some parts ending in such events."""
+    b = synth.generate_config("batched", n_events=2000)
+    ctx = g.Context(b.geom)
+    pipe = g.Pipeline(ctx, b, P)
+    pipe.run_batched()
+    ctx.check(what="tracks")
+    rng = np.random.default_rng(5)
+    for e in np.flatnonzero(rng.random(b.n_events) < 0.33):
+        pipe.tracks.found[int(b.trk_off[e]):int(b.trk_off[e + 1])] = 0
+    pipe.tracks.found[int(b.trk_off[b.n_events - 40]):int(b.trk_off[b.n_events])] = 0
+    tracks = g.tracks_to_numpy(pipe.tracks, b.n_tracks)
+    n = int(tracks["found"].sum())
+    out = g.CompactTracks.allocate(n)
+    off = torch.full((b.n_events + 1,), -7, dtype=torch.int32, device="cuda")
+    g.ut_consolidate(ctx, pipe.velo.trk_off, b.n_events, pipe.tracks, out, off)
+    ctx.check(what="consolidation")
+    ref, ref_off = oracle.consolidate(tracks, b.trk_off)
+    assert np.array_equal(off.cpu().numpy().view(np.uint32), ref_off)
+    _same(g.compact_to_numpy(out, n), ref, n)
+    ctx.close()
+
+
 def test_events_without_tracks(g):
     b = synth.generate(n_events=33, n_sectors=8, tracks=0, hits=3, seed=8)
     ctx = g.Context(b.geom)
