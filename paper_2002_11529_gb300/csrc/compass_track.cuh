@@ -851,7 +851,6 @@ __device__ __forceinline__ void eval_queued(const FindArgs& A, GroupHead* wh, co
         V.ft = ft;
         V.X = X;
         V.st = A.status;
-    V.st = A.status;
         V.off = off;
         V.S = A.S;
 #pragma unroll
@@ -928,8 +927,6 @@ __device__ void warp_search(const FindArgs& A, GroupHead* wh, const FitTable* ft
             V.h = h;
             V.X = X;
             V.st = A.status;
-        V.st = A.status;
-    V.st = A.status;
             V.off = off;
             V.S = A.S;
             V.hi[la] = h->hi[la];
