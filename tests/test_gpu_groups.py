@@ -27,6 +27,9 @@ CASES = {
     # 4 x 128 x 8 keys: the most the layout takes (fewer warp tables fit)
     "max_keys": dict(n_events=5, n_columns=31, rows=8, n_groups=128, tracks=100, hits=3000, seed=12),
     "one_event_dense": dict(n_events=1, tracks=200, hits=6000, seed=13),
+    # events with fewer hits than warps (empty and short chunks), and empty events
+    "sparse": dict(n_events=6, tracks=1, hits=5, seed=21),
+    "empty": dict(n_events=6, tracks=0, hits=0, seed=22),
 }
 
 
