@@ -66,6 +66,8 @@ BATCHES = {
     "dense": lambda: synth.generate(n_events=5, n_sectors=4, tracks=20, hits=3000, seed=7),
     # empty events in between
     "sparse": lambda: synth.generate(n_events=33, n_sectors=8, tracks=0, hits=3, seed=8),
+    # more than 1024 banks per event (the sorted maps hold the bank in 16 bits)
+    "wide600": lambda: synth.generate(n_events=8, n_sectors=600, tracks=100, hits=6000, seed=17),
 }
 
 
