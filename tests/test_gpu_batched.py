@@ -56,6 +56,19 @@ def test_batched_launch_shapes(g, tpw, block):
     check_against_oracle(g, pipe, b)
 
 
+@pytest.mark.parametrize("tpw,block", [(4, 256), (8, 800)])
+def test_batched_more_than_1024_banks(g, tpw, block):
+    """600 sectors per layer (2400 banks per event): the sorted decode maps of
+    the persistent kernel hold banks above 1023."""
+    b = synth.generate(n_events=8, n_sectors=600, tracks=100, hits=6000, seed=17)
+    ctx = g.Context(b.geom)
+    pipe = g.Pipeline(ctx, b, P)
+    pipe.run_batched(g.LaunchConfig(tpw, block, 8192, 8192))
+    ctx.check(what="batched")
+    check_against_oracle(g, pipe, b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("block", [544, 672, 800])
 def test_batched_large_blocks(g, block):
     """One block per SM of up to 25 warps (8 tracks per warp), on uneven
