@@ -61,6 +61,8 @@ __device__ __forceinline__ void batched_body(const DecodeArgs& D, const FindArgs
     __shared__ int s_event;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t warp_tot[kMaxDecodeThreads / 32];
+    __shared__ uint16_t list16[kMapList], listw[kMapList];
+    __shared__ int nlist[2];
 
     const int tid = threadIdx.x;
     const int B = 4 * D.S;
@@ -82,6 +84,9 @@ __device__ __forceinline__ void batched_body(const DecodeArgs& D, const FindArgs
     sm.warp_tot = warp_tot;
     sm.bmap = D.map_cap ? reinterpret_cast<uint16_t*>(smem + L.map_byte0) : nullptr;
     sm.srcmap = sm.bmap ? sm.bmap + D.map_cap : nullptr;
+    sm.list16 = list16;
+    sm.listw = listw;
+    sm.nlist = nlist;
     float* sx = reinterpret_cast<float*>(smem + L.sx_byte0);
     GroupHead* heads = reinterpret_cast<GroupHead*>(smem + L.union_byte0);
     PairQueue* Q = reinterpret_cast<PairQueue*>(smem + L.queues_byte0) + tid / 32;
@@ -143,7 +148,7 @@ static int launch_batched(const DecodeArgs& D, const FindArgs& A, int block, con
     const int nt = NT ? NT : block;
     const BatchedLayout L = batched_layout(B, D.stage_words, A.x_cap, D.map_cap, nt / G, nt / 32);
     const size_t smem = L.total;
-    if (smem + 1024 > (size_t)ctx->smem_optin) return UT_ERR_ARG;  // shape does not fit (static smem included)
+    if (smem + 2048 > (size_t)ctx->smem_optin) return UT_ERR_ARG;  // shape does not fit (static smem included)
     void (*kern)(const DecodeArgs, const FindArgs) = nullptr;
     if constexpr (NT > 0)
         kern = ut_batched_kernel<G, NT>;

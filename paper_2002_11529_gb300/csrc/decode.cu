@@ -21,12 +21,14 @@ namespace utc {
 
 constexpr int kDecodeThreads = 256;
 template <bool SORT>
-__global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeArgs a) {
+__global__ void __launch_bounds__(kDecodeThreads, SORT ? 3 : 6) ut_decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ int s_event;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t warp_tot[kMaxDecodeThreads / 32];
+    __shared__ uint16_t list16[SORT ? kMapList : 1], listw[SORT ? kMapList : 1];
+    __shared__ int nlist[2];
 
     const int tid = threadIdx.x;
     const int B = 4 * a.S;
@@ -45,6 +47,9 @@ __global__ void __launch_bounds__(kDecodeThreads) ut_decode_kernel(const DecodeA
     // output position (events of at most map_cap hits)
     sm.bmap = a.map_cap ? reinterpret_cast<uint16_t*>(smem + stage_byte0 + (size_t)a.stage_words * 4) : nullptr;
     sm.srcmap = SORT && sm.bmap ? sm.bmap + a.map_cap : nullptr;
+    sm.list16 = SORT ? list16 : nullptr;
+    sm.listw = SORT ? listw : nullptr;
+    sm.nlist = SORT ? nlist : nullptr;
 
     if (tid == 0) {
         s_event = (int)atomicAdd(a.ticket, 1u);

@@ -223,7 +223,13 @@ struct DecodeSmem {
     uint32_t* warp_tot;          // kMaxDecodeThreads / 32
     uint16_t* bmap;              // map_cap: bank of each hit (null: mapped path off)
     uint16_t* srcmap;            // map_cap: hit written at each output position
+    uint16_t* list16;            // kMapList: banks of 9..kNetBank hits (null: sorted where met)
+    uint16_t* listw;             // kMapList: banks of kNetBank+1..kSmallBank hits
+    int* nlist;                  // 2 counters of the lists
 };
+
+// Capacity of each of the two bank lists of the sorted maps.
+constexpr int kMapList = 256;
 
 __device__ __forceinline__ const uint16_t* bank_words(const uint32_t* evw, int b) {
     return reinterpret_cast<const uint16_t*>(evw + evw[b] + 1);
@@ -401,14 +407,17 @@ __device__ __forceinline__ void warp_sort_bank(const uint16_t* w16, uint32_t wpo
 }
 
 // Shared-memory maps of an event of at most map_cap hits, built before its
-// global base is known.  bmap[i] = bank of output position i.  SORT
-// (B <= 1024): srcmap[i] = position, in the event's 16-bit words, of the
-// word at output position i.  One thread per bank: a bank of at most
-// kNetBank hits is sorted at once by a sorting network in registers; the
-// warp then sorts together, one after the other, its banks of up to
-// kSmallBank hits (warp_sort_bank).  Larger banks (any_big: the event has
-// some) are ranked by rank_big_banks straight into srcmap.  The maps are
-// complete after the next __syncthreads of the caller.
+// global base is known.  bmap[i] = bank of output position i.  SORT:
+// srcmap[i] = position, in the event's 16-bit words, of the word at output
+// position i.  One thread per bank: a bank of at most 8 hits is sorted at
+// once by a sorting network in registers.  With the block's bank lists
+// (sm.list16, sm.listw), banks of 9..kNetBank hits and of up to kSmallBank
+// hits are listed, and after a barrier sorted by networks of 16 keys one
+// per thread and by whole warps (warp_sort_bank), spread over all warps;
+// without them (or when a list is full) they are sorted by the thread, or
+// the warp, that meets them.  Larger banks (any_big: the event has some)
+// are ranked by rank_big_banks straight into srcmap.  The maps are complete
+// after the next __syncthreads of the caller.
 template <bool SORT>
 __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint32_t* evw, bool any_big,
                           uint64_t nw) {
@@ -420,6 +429,8 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
     const int lane = tid & 31, wt0 = tid - lane;
     const int L = min(32, nt - wt0);  // lanes of this warp
     const uint32_t wmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+    const bool lists = SORT && sm.list16 != nullptr;
+    const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw);
     // the same number of rounds for every lane of a warp (warp-wide sorts)
     for (int k0 = 0; wt0 + k0 < B; k0 += nt) {
         const int b = tid + k0;
@@ -429,15 +440,17 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
             if (chk(j0 + n <= a.map_cap, a.status, 104)) {
                 if (SORT && n <= (uint32_t)kSmallBank) {
                     if (chk((uint64_t)evw[b] + 1 + (n + 1) / 2 <= nw, a.status, 110)) {
-                        if (n <= (uint32_t)kNetBank) {
-                            const uint32_t wpos0 = 2u * (evw[b] + 1u);
-                            const uint16_t* w16 = reinterpret_cast<const uint16_t*>(evw) + wpos0;
-                            if (n <= 8)
-                                sort_small_bank<8>(w16, wpos0, n, b, j0, bmap, srcm);
-                            else
-                                sort_small_bank<kNetBank>(w16, wpos0, n, b, j0, bmap, srcm);
+                        const uint32_t wpos0 = 2u * (evw[b] + 1u);
+                        if (n <= 8) {
+                            sort_small_bank<8>(w16 + wpos0, wpos0, n, b, j0, bmap, srcm);
+                        } else if (n <= (uint32_t)kNetBank) {
+                            const int idx = lists ? atomicAdd(&sm.nlist[0], 1) : kMapList;
+                            if (idx < kMapList) sm.list16[idx] = (uint16_t)b;
+                            else sort_small_bank<kNetBank>(w16 + wpos0, wpos0, n, b, j0, bmap, srcm);
                         } else {
-                            coop = true;
+                            const int idx = lists ? atomicAdd(&sm.nlist[1], 1) : kMapList;
+                            if (idx < kMapList) sm.listw[idx] = (uint16_t)b;
+                            else coop = true;
                         }
                     }
                 } else {
@@ -453,12 +466,34 @@ __device__ void map_event(const DecodeArgs& a, const DecodeSmem& sm, const uint3
                 const int bb = wt0 + k0 + src;
                 const uint32_t j0 = off[bb], n = off[bb + 1] - j0;
                 const uint32_t wpos0 = 2u * (evw[bb] + 1u);
-                warp_sort_bank(reinterpret_cast<const uint16_t*>(evw) + wpos0, wpos0, n, bb, j0, bmap, srcm, lane, L,
-                               wmask);
+                warp_sort_bank(w16 + wpos0, wpos0, n, bb, j0, bmap, srcm, lane, L, wmask);
             }
         }
     }
     if constexpr (SORT) {
+        if (lists) {
+            // The listed banks, spread over all warps: the hot sectors are
+            // neighbours, and sorted where met they would fall to one or
+            // two warps.  Banks of 9..kNetBank hits: one per thread, entry
+            // lane * warps + warp (so each warp takes some); larger ones: one
+            // per warp at a time.
+            __syncthreads();
+            const int n16 = min(sm.nlist[0], kMapList), nwl = min(sm.nlist[1], kMapList);
+            const int nwarps = (nt + 31) >> 5, w = tid >> 5;
+            const int slot = (nt & 31) == 0 ? lane * nwarps + w : tid;
+            for (int i = slot; i < n16; i += nt) {
+                const int b = sm.list16[i];
+                const uint32_t j0 = off[b], n = off[b + 1] - j0;
+                const uint32_t wpos0 = 2u * (evw[b] + 1u);
+                sort_small_bank<kNetBank>(w16 + wpos0, wpos0, n, b, j0, bmap, srcm);
+            }
+            for (int i = w; i < nwl; i += nwarps) {
+                const int b = sm.listw[i];
+                const uint32_t j0 = off[b], n = off[b + 1] - j0;
+                const uint32_t wpos0 = 2u * (evw[b] + 1u);
+                warp_sort_bank(w16 + wpos0, wpos0, n, b, j0, bmap, srcm, lane, L, wmask);
+            }
+        }
         if (any_big)
             rank_big_banks(off, B, evw, sm.bigcnt, [&](int b, uint32_t pos, uint32_t k, uint32_t) {
                 srcm[off[b] + pos] = (uint16_t)(2u * (evw[b] + 1u) + k);
@@ -561,6 +596,8 @@ __device__ void decode_event(const DecodeArgs& a, int e, const DecodeSmem& sm, u
     const bool ev_ok = we >= ws && we <= a.n_words && (we - ws) >= (uint64_t)B;
     const uint64_t nw = ev_ok ? we - ws : 0;
     const uint32_t* evw = a.raw + (ev_ok ? ws : 0);
+
+    if (SORT && sm.nlist != nullptr && tid == 0) sm.nlist[0] = sm.nlist[1] = 0;  // read after the scan's barriers
 
     // Stage the whole event (16-byte aligned superset) with one bulk copy.
     // After a copy that did not complete in time the block stops using the
